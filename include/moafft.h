@@ -1,0 +1,156 @@
+/*
+ * moafft.h -- C ABI of the GB300-native MoA / psi-calculus radix-2 FFT.
+ *
+ * The operation (Mullin & Raynolds, "Conformal Computing", Fig. vanloan_fft):
+ * input x in C^n with n = 2^t, t >= 0; output the discrete Fourier transform
+ *     X_k = sum_{j<n} x_j * exp(s * 2*pi*i * j*k / n),   0 <= k < n,
+ * computed as a radix-2 Cooley-Tukey FFT whose stages are grouped into
+ * passes over a dimension-lifted view of the signal (Ch.3: stages inside
+ * blocks, reshape-transposes between groups of stages, one final transpose
+ * done by addressing, Eq. xihyper).
+ *
+ * Data layout (every entry point): interleaved complex (re, im) pairs,
+ * element type float2 (FFT_C64) or double2 (FFT_C128); a batch of
+ * transforms is stored transform after transform, each contiguous, so
+ * transform b starts at element b*n.  Pointers passed to fft_exec* are
+ * device pointers owned by the caller, aligned to the element size (8 B for
+ * C64, 16 B for C128).  Host pointers are rejected with FFT_ERR_ARG.
+ *
+ * Errors: every function returns FFT_OK (0) or a negative fft_status; no
+ * C++ exception crosses this boundary.  fft_last_error() returns a
+ * thread-local message describing the most recent failure of the calling
+ * thread.  Asynchronous kernel faults surface as FFT_ERR_CUDA on a later
+ * call that synchronises.
+ *
+ * Threading: a plan may be executed from one host thread at a time; two
+ * executions of the same plan on different streams must not overlap in time,
+ * because they share the plan's workspace.
+ */
+#ifndef MOAFFT_H
+#define MOAFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan_s *fft_plan_t;
+
+/* Element type: interleaved complex single (8 B) or double (16 B). */
+typedef enum { FFT_C64 = 0, FFT_C128 = 1 } fft_dtype;
+
+/* Exponent sign s of the transform.  FFT_FORWARD: s = -1, unscaled.
+ * FFT_INVERSE: s = +1, result scaled by 1/n, so inverse(forward(x)) = x.
+ * (The paper's fftpsirad2 weights use exp(+2*pi*i*row/L); its general-radix
+ * code uses exp(-2*pi*i/base); forward here follows the latter.) */
+typedef enum { FFT_FORWARD = -1, FFT_INVERSE = 1 } fft_dir;
+
+/* Arithmetic form of the butterfly stages.
+ * FFT_FORM_PLAIN: radix-2^k butterflies in the element precision (FP64 for
+ *   C128, FP32 for C64).
+ * FFT_FORM_TC_FP16 / FFT_FORM_TC_BF16 (C64 only): radix-16 DFT stages as
+ *   tensor-core matrix products with split (hi + lo) FP16 or BF16 operands
+ *   and FP32 accumulation (the radix-n DFT of the general-radix routine,
+ *   Fig. radnbutterfly, written as a dense product). */
+typedef enum {
+    FFT_FORM_PLAIN = 0,
+    FFT_FORM_TC_FP16 = 1,
+    FFT_FORM_TC_BF16 = 2
+} fft_form;
+
+typedef enum {
+    FFT_OK = 0,
+    FFT_ERR_ARG = -1,         /* null pointer, n < 1, batch < 1, bad schedule text */
+    FFT_ERR_NOT_POW2 = -2,    /* n is not 2^t (the paper's domain, Fig. vanloan_fft) */
+    FFT_ERR_DTYPE = -3,       /* unknown dtype or direction */
+    FFT_ERR_ALIAS = -4,       /* in and out overlap without being identical */
+    FFT_ERR_ALLOC = -5,       /* device allocation failed */
+    FFT_ERR_CUDA = -6,        /* a CUDA runtime call or kernel failed */
+    FFT_ERR_TIMEOUT = -7,     /* a bounded device-side wait gave up */
+    FFT_ERR_UNSUPPORTED = -8  /* valid request this build does not provide */
+} fft_status;
+
+/* Create a plan for `batch` transforms of length n.  Allocates the device
+ * twiddle tables (generated on the GPU in FP64 with sincospi) and the pass
+ * workspace; the plan owns both until fft_destroy.  *out is set to NULL on
+ * failure.  Cite: Fig. vanloan_fft (input/output); Ch.3 (the blocking is a
+ * run-time parameter of the plan). */
+int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir);
+
+/* As fft_plan, with an arithmetic form and an optional schedule string.
+ * schedule == NULL or "" picks the built-in heuristic (or a cached
+ * autotuner choice); "auto" runs the autotuner now (times candidate
+ * schedules on the plan's own buffers, then caches the winner).  Otherwise
+ * the string lists the log2 radix of each HBM pass, comma separated, each
+ * optionally followed by "@W" (columns per thread block), e.g. "10,10" or
+ * "8@8,8@8,8@8".  The radices must sum to log2 n.  The paper lets the user
+ * choose the block size c at run time (Ch.2 "specify the blocking size at
+ * run time"); a pass of log2 radix r is a group of r radix-2 stages. */
+int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,
+                fft_form form, const char *schedule);
+
+/* Uneven batch: `count` transforms of power-of-two lengths sizes[i] (host
+ * array, copied), packed back to back in the order given (transform i starts
+ * at element sum_{j<i} sizes[j]).  Executed as one persistent, graph-captured
+ * launch sequence.  Cite: Ch.3 "The Number of Reshape-Transpose Operations"
+ * (the schedule is chosen per length). */
+int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t count, fft_dtype dt,
+                  fft_dir dir);
+
+/* Run the plan's transform: out = F(in) for every transform of the batch,
+ * on `cuda_stream` (a cudaStream_t; NULL means the legacy default stream).
+ * in == out is allowed (in place); any other overlap returns FFT_ERR_ALIAS.
+ * Asynchronous: returns after enqueueing the kernels. */
+int fft_exec(fft_plan_t p, const void *in, void *out, void *cuda_stream);
+
+/* Apply the adjoint (conjugate transpose) of the plan's operator.  For a
+ * FORWARD plan this is the unscaled s = +1 transform; for an INVERSE plan the
+ * (1/n)-scaled s = -1 transform.  Same layout, aliasing and stream rules as
+ * fft_exec.  Cite: Fig. vanloan_fft (the adjoint of each B_L is the
+ * conjugate transpose of the butterfly block). */
+int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream);
+
+/* Release everything the plan owns.  NULL is a no-op.  Synchronises the
+ * device before freeing. */
+int fft_destroy(fft_plan_t p);
+
+/* Thread-local text of the calling thread's last error ("" if none). */
+const char *fft_last_error(void);
+
+/* ---- introspection and host-side helpers (no GPU work) ------------------ */
+
+/* Write a one-line JSON description of the schedule the library would use
+ * for (n, dt, form, schedule) into buf (NUL-terminated, truncated to len).
+ * Pure host logic: no device allocation or launch. */
+int fft_describe_schedule(int64_t n, fft_dtype dt, fft_form form, const char *schedule,
+                          char *buf, int64_t len);
+
+/* One-line JSON description of a plan (passes, radices, workspace bytes,
+ * kernel launches per execution). */
+int fft_plan_describe(fft_plan_t p, char *buf, int64_t len);
+
+/* Number of kernel launches one fft_exec of this plan performs. */
+int64_t fft_plan_launches(fft_plan_t p);
+
+/* Bytes of device workspace the plan holds (twiddle tables excluded). */
+int64_t fft_plan_workspace_bytes(fft_plan_t p);
+
+/* Replace the device allocator used by subsequent fft_plan* calls.  alloc
+ * returns a device pointer of at least `bytes` or NULL; release frees it.
+ * Passing NULL for both restores cudaMalloc/cudaFree.  ctx is passed back
+ * unchanged.  Used to route plan memory through a caller's pool and to
+ * inject allocation failures in tests. */
+typedef void *(*fft_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*fft_free_fn)(void *ptr, void *ctx);
+int fft_set_allocator(fft_alloc_fn alloc, fft_free_fn release, void *ctx);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOAFFT_H */

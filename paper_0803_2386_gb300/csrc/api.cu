@@ -1,0 +1,553 @@
+// api.cu -- the C ABI (include/moafft.h): plans, schedules, execution.
+//
+// A plan fixes the dimension lifting of the signal: log2 n radix-2 stages
+// (Fig. vanloan_fft) are grouped into HBM passes of log2 R stages each
+// (Ch.3: groups of log2 c stages between reshape-transposes, with c chosen
+// at run time).  Inside a pass the group is split again into register
+// codelets of <= 4 stages (radix 16).  The plan owns the weight tables and
+// the workspace that carries the data between passes.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace moafft;
+
+// --------------------------------------------------------------- errors ---
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+static int fail_cuda(cudaError_t e, const char *what)
+{
+    return fail(FFT_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ allocator ---
+
+static std::mutex g_alloc_mu;
+static fft_alloc_fn g_alloc = nullptr;
+static fft_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+struct DevBuf {
+    void *ptr = nullptr;
+    fft_free_fn release = nullptr;  // nullptr: cudaFree
+    void *ctx = nullptr;
+};
+
+static int dev_alloc(DevBuf &b, size_t bytes, const char *what)
+{
+    fft_alloc_fn a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        b.release = g_free;
+        b.ctx = g_alloc_ctx;
+    }
+    if (bytes == 0) bytes = 16;
+    if (a) {
+        b.ptr = a(bytes, b.ctx);
+        if (!b.ptr) return fail(FFT_ERR_ALLOC, "allocator returned NULL for %s (%zu bytes)", what, bytes);
+        return FFT_OK;
+    }
+    b.release = nullptr;
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        cudaGetLastError();
+        if (e == cudaErrorMemoryAllocation)
+            return fail(FFT_ERR_ALLOC, "cudaMalloc of %zu bytes for %s failed", bytes, what);
+        return fail_cuda(e, "cudaMalloc");
+    }
+    return FFT_OK;
+}
+
+static void dev_free(DevBuf &b)
+{
+    if (!b.ptr) return;
+    if (b.release) b.release(b.ptr, b.ctx);
+    else cudaFree(b.ptr);
+    b.ptr = nullptr;
+}
+
+extern "C" int fft_set_allocator(fft_alloc_fn alloc, fft_free_fn release, void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(FFT_ERR_ARG, "fft_set_allocator: give both functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return FFT_OK;
+}
+
+// ------------------------------------------------------------- schedule ---
+
+static int exact_log2(int64_t n)
+{
+    if (n < 1 || (n & (n - 1)) != 0) return -1;
+    int t = 0;
+    while (((int64_t)1 << t) < n) t++;
+    return t;
+}
+
+// elements a tile may hold (shared memory budget of 64 KiB per CTA)
+static int tile_budget(fft_dtype dt) { return dt == FFT_C128 ? 4096 : 8192; }
+static int max_tile_log(fft_dtype dt) { return dt == FFT_C128 ? 11 : 11; }
+static size_t elem_bytes(fft_dtype dt) { return dt == FFT_C128 ? 16 : 8; }
+
+static void split_subpasses(PassDesc &p)
+{
+    int r = p.log_r;
+    p.nsub = 0;
+    if (r % 4) p.sub_log[p.nsub++] = r % 4;
+    for (int k = 0; k < r / 4; k++) p.sub_log[p.nsub++] = 4;
+}
+
+// Fill in A, B and the tile widths once the radices are known.
+static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
+{
+    int64_t A = 1;
+    int used = 0;
+    for (int i = 0; i < s.npass; i++) used += s.pass[i].log_r;
+    if (used != s.t) return fail(FFT_ERR_ARG, "schedule radices sum to %d, log2 n is %d", used, s.t);
+    for (int i = 0; i < s.npass; i++) {
+        PassDesc &p = s.pass[i];
+        int64_t R = (int64_t)1 << p.log_r;
+        p.A = A;
+        p.B = s.n / (A * R);
+        A *= R;
+        const bool last = (i == s.npass - 1);
+        int64_t span = last ? (p.A > 1 ? p.A : INT64_MAX) : p.B;
+        int64_t w;
+        if (req_width && req_width[i] > 0) {
+            w = req_width[i];
+            if (exact_log2(w) < 0) return fail(FFT_ERR_ARG, "tile width %lld is not a power of two", (long long)w);
+        } else {
+            w = std::max<int64_t>(1, tile_budget(dt) / R);
+            w = std::min<int64_t>(w, last && p.A == 1 ? 1024 : 16);
+        }
+        w = std::min<int64_t>(w, span);
+        if (R * w > 2 * tile_budget(dt))
+            return fail(FFT_ERR_ARG, "tile of %lld x %lld elements exceeds shared memory", (long long)R,
+                        (long long)w);
+        p.width = (int)w;
+        split_subpasses(p);
+        p.tw_m = R * p.B;
+        p.tw_lo_bits = 0;
+        if (!last) {
+            int lm = exact_log2(p.tw_m);
+            int direct_max = dt == FFT_C128 ? 20 : 21;
+            if (lm > direct_max) p.tw_lo_bits = (lm + 1) / 2;
+        }
+    }
+    return FFT_OK;
+}
+
+static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
+{
+    s = Schedule();
+    s.n = n;
+    s.t = exact_log2(n);
+    int mt = max_tile_log(dt);
+    int g = s.t == 0 ? 1 : (s.t + mt - 1) / mt;
+    s.npass = g;
+    for (int i = 0; i < g; i++) s.pass[i].log_r = s.t / g + (i < s.t % g ? 1 : 0);
+    return finish_schedule(s, dt, nullptr);
+}
+
+// "r0[@w0],r1[@w1],..."
+static int parse_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text)
+{
+    s = Schedule();
+    s.n = n;
+    s.t = exact_log2(n);
+    int widths[kMaxPasses] = {0};
+    const char *p = text;
+    int np = 0;
+    while (*p) {
+        if (np >= kMaxPasses) return fail(FFT_ERR_ARG, "schedule '%s': more than %d passes", text, kMaxPasses);
+        char *end;
+        long r = strtol(p, &end, 10);
+        if (end == p || r < 0 || r > 13) return fail(FFT_ERR_ARG, "schedule '%s': bad radix at '%s'", text, p);
+        s.pass[np].log_r = (int)r;
+        p = end;
+        if (*p == '@') {
+            long w = strtol(p + 1, &end, 10);
+            if (end == p + 1 || w < 1 || w > 4096) return fail(FFT_ERR_ARG, "schedule '%s': bad width", text);
+            widths[np] = (int)w;
+            p = end;
+        }
+        np++;
+        if (*p == ',') {
+            p++;
+            if (!*p) return fail(FFT_ERR_ARG, "schedule '%s': trailing comma", text);
+        } else if (*p) {
+            return fail(FFT_ERR_ARG, "schedule '%s': unexpected '%c'", text, *p);
+        }
+    }
+    if (np == 0) return fail(FFT_ERR_ARG, "schedule '%s' is empty", text);
+    s.npass = np;
+    return finish_schedule(s, dt, widths);
+}
+
+// Schedule text: "" / "auto" (heuristic) or a pass list, optionally followed
+// by ";chunk=K" (transforms per workspace round of a multi-pass plan).
+static int build_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text, int64_t *chunk)
+{
+    if (chunk) *chunk = 0;
+    std::string body = text ? text : "";
+    size_t semi = body.find(';');
+    if (semi != std::string::npos) {
+        std::string opt = body.substr(semi + 1);
+        body = body.substr(0, semi);
+        if (opt.rfind("chunk=", 0) != 0) return fail(FFT_ERR_ARG, "schedule option '%s' unknown", opt.c_str());
+        char *end;
+        long long k = strtoll(opt.c_str() + 6, &end, 10);
+        if (*end || k < 1) return fail(FFT_ERR_ARG, "schedule option '%s' is not a positive count", opt.c_str());
+        if (chunk) *chunk = k;
+    }
+    if (body.empty() || body == "auto") return default_schedule(s, n, dt);
+    return parse_schedule(s, n, dt, body.c_str());
+}
+
+static std::string schedule_json(const Schedule &s)
+{
+    std::string j = "{\"n\": " + std::to_string(s.n) + ", \"passes\": [";
+    for (int i = 0; i < s.npass; i++) {
+        const PassDesc &p = s.pass[i];
+        char buf[256];
+        std::string subs;
+        for (int k = 0; k < p.nsub; k++) subs += (k ? "," : "") + std::to_string(p.sub_log[k]);
+        snprintf(buf, sizeof buf,
+                 "%s{\"log_r\": %d, \"A\": %lld, \"B\": %lld, \"width\": %d, \"sub_log\": [%s], "
+                 "\"tw_m\": %lld, \"tw_lo_bits\": %d}",
+                 i ? ", " : "", p.log_r, (long long)p.A, (long long)p.B, p.width, subs.c_str(),
+                 (long long)p.tw_m, p.tw_lo_bits);
+        j += buf;
+    }
+    j += "]}";
+    return j;
+}
+
+// ---------------------------------------------------------------- plans ---
+
+struct fft_plan_s {
+    int64_t n = 0, batch = 0;
+    fft_dtype dt = FFT_C64;
+    fft_dir dir = FFT_FORWARD;
+    fft_form form = FFT_FORM_PLAIN;
+    Schedule sched;
+    int64_t chunk = 1;  // transforms per workspace round
+    DevBuf tw;          // twiddle arena
+    DevBuf ws;          // inter-pass workspace
+    int64_t ws_bytes = 0;
+    int device = 0;
+};
+
+namespace moafft {
+int pass_threads(const PassArgs &a)
+{
+    int64_t t = ((int64_t)1 << a.log_r) * a.width / 16;
+    if (t < 32) t = 32;
+    if (t > 256) t = 256;
+    return (int)((t + 31) / 32 * 32);
+}
+
+size_t pass_smem_bytes(const PassArgs &a, size_t eb)
+{
+    size_t e = ((size_t)1 << a.log_r) * (size_t)a.width;
+    return (e + e / 32 + 1) * eb;
+}
+}  // namespace moafft
+
+static int64_t launches_per_exec(const fft_plan_s *p)
+{
+    if (p->sched.npass == 1) return 1;
+    int64_t chunks = (p->batch + p->chunk - 1) / p->chunk;
+    return chunks * p->sched.npass;
+}
+
+static int make_tables(fft_plan_s *p)
+{
+    // arena layout: for each pass, tile table (R entries), then pass table(s)
+    size_t eb = elem_bytes(p->dt);
+    size_t off = 0;
+    for (int i = 0; i < p->sched.npass; i++) {
+        PassDesc &d = p->sched.pass[i];
+        d.tw_tile_off = off;
+        off += (size_t)1 << d.log_r;
+        if (i < p->sched.npass - 1) {
+            d.tw_pass_off = off;
+            if (d.tw_lo_bits == 0) off += (size_t)d.tw_m;
+            else {
+                off += (size_t)1 << d.tw_lo_bits;
+                d.tw_hi_off = off;
+                off += (size_t)(d.tw_m >> d.tw_lo_bits);
+            }
+        }
+    }
+    int st = dev_alloc(p->tw, off * eb, "twiddle tables");
+    if (st != FFT_OK) return st;
+    for (int i = 0; i < p->sched.npass; i++) {
+        PassDesc &d = p->sched.pass[i];
+        int64_t R = (int64_t)1 << d.log_r;
+        auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
+            if (p->dt == FFT_C128)
+                return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
+            return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
+        };
+        cudaError_t e = gen(d.tw_tile_off, R, R, 1);
+        if (e == cudaSuccess && i < p->sched.npass - 1) {
+            if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
+            else {
+                e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
+                if (e == cudaSuccess)
+                    e = gen(d.tw_hi_off, d.tw_m >> d.tw_lo_bits, d.tw_m, (int64_t)1 << d.tw_lo_bits);
+            }
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "twiddle generation (sync)");
+    return FFT_OK;
+}
+
+static int check_common(int64_t n, fft_dtype dt, fft_dir dir)
+{
+    if (dt != FFT_C64 && dt != FFT_C128) return fail(FFT_ERR_DTYPE, "unknown dtype %d", (int)dt);
+    if (dir != FFT_FORWARD && dir != FFT_INVERSE) return fail(FFT_ERR_DTYPE, "unknown direction %d", (int)dir);
+    if (n < 1) return fail(FFT_ERR_ARG, "n = %lld < 1", (long long)n);
+    if (exact_log2(n) < 0) return fail(FFT_ERR_NOT_POW2, "n = %lld is not a power of two", (long long)n);
+    if (exact_log2(n) > 30) return fail(FFT_ERR_UNSUPPORTED, "n = 2^%d exceeds 2^30", exact_log2(n));
+    return FFT_OK;
+}
+
+extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,
+                           fft_form form, const char *schedule)
+{
+    if (!out) return fail(FFT_ERR_ARG, "fft_plan: out is NULL");
+    *out = nullptr;
+    int st = check_common(n, dt, dir);
+    if (st != FFT_OK) return st;
+    if (batch < 1) return fail(FFT_ERR_ARG, "batch = %lld < 1", (long long)batch);
+    if (form != FFT_FORM_PLAIN && form != FFT_FORM_TC_FP16 && form != FFT_FORM_TC_BF16)
+        return fail(FFT_ERR_ARG, "unknown form %d", (int)form);
+    if (form != FFT_FORM_PLAIN)
+        return fail(FFT_ERR_UNSUPPORTED, "tensor-core form not available in this build");
+    fft_plan_s *p = new (std::nothrow) fft_plan_s();
+    if (!p) return fail(FFT_ERR_ALLOC, "host allocation of the plan failed");
+    p->n = n;
+    p->batch = batch;
+    p->dt = dt;
+    p->dir = dir;
+    p->form = form;
+    int64_t req_chunk = 0;
+    st = build_schedule(p->sched, n, dt, schedule, &req_chunk);
+    if (st != FFT_OK) {
+        delete p;
+        return st;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail_cuda(e, "cudaGetDevice");
+    }
+    size_t eb = elem_bytes(dt);
+    if (p->sched.npass > 1) {
+        const int64_t target = (int64_t)32 << 20;  // bytes per workspace round (L2-resident)
+        p->chunk = std::max<int64_t>(1, std::min<int64_t>(batch, target / (n * (int64_t)eb)));
+        if (req_chunk > 0) p->chunk = std::min<int64_t>(batch, req_chunk);
+        p->ws_bytes = p->chunk * n * (int64_t)eb;
+        st = dev_alloc(p->ws, (size_t)p->ws_bytes, "workspace");
+        if (st != FFT_OK) {
+            delete p;
+            return st;
+        }
+    } else {
+        p->chunk = batch;
+    }
+    st = make_tables(p);
+    if (st != FFT_OK) {
+        dev_free(p->ws);
+        dev_free(p->tw);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return FFT_OK;
+}
+
+extern "C" int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir)
+{
+    return fft_plan_ex(out, n, batch, dt, dir, FFT_FORM_PLAIN, nullptr);
+}
+
+extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t count, fft_dtype dt,
+                             fft_dir dir)
+{
+    if (!out) return fail(FFT_ERR_ARG, "fft_plan_many: out is NULL");
+    *out = nullptr;
+    if (!sizes || count < 1) return fail(FFT_ERR_ARG, "fft_plan_many: empty size list");
+    for (int64_t i = 0; i < count; i++) {
+        int st = check_common(sizes[i], dt, dir);
+        if (st != FFT_OK) return st;
+    }
+    return fail(FFT_ERR_UNSUPPORTED, "fft_plan_many not available in this build");
+}
+
+extern "C" int fft_destroy(fft_plan_t p)
+{
+    if (!p) return FFT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    dev_free(p->ws);
+    dev_free(p->tw);
+    delete p;
+    if (e != cudaSuccess) return fail_cuda(e, "fft_destroy (sync)");
+    return FFT_OK;
+}
+
+// ------------------------------------------------------------ execution ---
+
+static int check_device_ptr(const void *ptr, size_t align, const char *what)
+{
+    if (!ptr) return fail(FFT_ERR_ARG, "%s is NULL", what);
+    if ((uintptr_t)ptr % align) return fail(FFT_ERR_ARG, "%s is not %zu-byte aligned", what, align);
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FFT_ERR_ARG, "%s is not a device pointer (%s)", what, cudaGetErrorName(e));
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(FFT_ERR_ARG, "%s is not device memory", what);
+    return FFT_OK;
+}
+
+static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoint)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    size_t eb = elem_bytes(p->dt);
+    int st = check_device_ptr(in, eb, "in");
+    if (st != FFT_OK) return st;
+    st = check_device_ptr(out, eb, "out");
+    if (st != FFT_OK) return st;
+    const size_t bytes = (size_t)p->n * (size_t)p->batch * eb;
+    uintptr_t a0 = (uintptr_t)in, a1 = a0 + bytes, b0 = (uintptr_t)out, b1 = b0 + bytes;
+    if (in != out && a0 < b1 && b0 < a1)
+        return fail(FFT_ERR_ALIAS, "in and out overlap without being identical");
+
+    // direction and scaling: forward s=-1 unscaled, inverse s=+1 x 1/n;
+    // adjoint swaps the sign and keeps the scaling.
+    int sign = (int)p->dir;
+    if (adjoint) sign = -sign;
+    double scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const Schedule &S = p->sched;
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = p->n;
+    a.npass = S.npass;
+    for (int i = 0; i < S.npass; i++) a.pass_log[i] = S.pass[i].log_r;
+    for (int64_t c0 = 0; c0 < p->batch; c0 += p->chunk) {
+        int64_t cnt = std::min(p->chunk, p->batch - c0);
+        const char *src = (const char *)in + (size_t)c0 * p->n * eb;
+        char *dst = (char *)out + (size_t)c0 * p->n * eb;
+        for (int i = 0; i < S.npass; i++) {
+            const PassDesc &d = S.pass[i];
+            a.in = (i == 0) ? (const void *)src : p->ws.ptr;
+            a.out = (i == S.npass - 1) ? (void *)dst : p->ws.ptr;
+            a.count = cnt;
+            a.log_r = d.log_r;
+            a.width = d.width;
+            a.nsub = d.nsub;
+            for (int k = 0; k < kMaxSub; k++) a.sub_log[k] = d.sub_log[k];
+            a.A = d.A;
+            a.B = d.B;
+            a.is_last = (i == S.npass - 1);
+            a.tw_tile = (const char *)p->tw.ptr + d.tw_tile_off * eb;
+            a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
+            a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
+            a.tw_lo_bits = d.tw_lo_bits;
+            a.scale = a.is_last ? scale : 1.0;
+            cudaError_t e = p->dt == FFT_C128 ? launch_pass_f64(a, sign, s) : launch_pass_f32(a, sign, s);
+            if (e != cudaSuccess) return fail_cuda(e, "pass launch");
+        }
+    }
+    return FFT_OK;
+}
+
+extern "C" int fft_exec(fft_plan_t p, const void *in, void *out, void *cuda_stream)
+{
+    return run(p, in, out, cuda_stream, false);
+}
+
+extern "C" int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream)
+{
+    return run(p, in, out, cuda_stream, true);
+}
+
+// --------------------------------------------------------- introspection --
+
+extern "C" const char *fft_last_error(void) { return g_last_error.c_str(); }
+
+static int put(char *buf, int64_t len, const std::string &s)
+{
+    if (!buf || len < 1) return fail(FFT_ERR_ARG, "output buffer is NULL or empty");
+    size_t k = std::min<size_t>(s.size(), (size_t)len - 1);
+    memcpy(buf, s.data(), k);
+    buf[k] = 0;
+    return FFT_OK;
+}
+
+extern "C" int fft_describe_schedule(int64_t n, fft_dtype dt, fft_form form, const char *schedule,
+                                     char *buf, int64_t len)
+{
+    int st = check_common(n, dt, FFT_FORWARD);
+    if (st != FFT_OK) return st;
+    (void)form;
+    Schedule s;
+    st = build_schedule(s, n, dt, schedule, nullptr);
+    if (st != FFT_OK) return st;
+    return put(buf, len, schedule_json(s));
+}
+
+extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    std::string j = "{\"n\": " + std::to_string(p->n) + ", \"batch\": " + std::to_string(p->batch) +
+                    ", \"dtype\": \"" + (p->dt == FFT_C128 ? "c128" : "c64") + "\", \"chunk\": " +
+                    std::to_string(p->chunk) + ", \"workspace_bytes\": " + std::to_string(p->ws_bytes) +
+                    ", \"launches\": " + std::to_string(launches_per_exec(p)) +
+                    ", \"schedule\": " + schedule_json(p->sched) + "}";
+    return put(buf, len, j);
+}
+
+extern "C" int64_t fft_plan_launches(fft_plan_t p) { return p ? launches_per_exec(p) : 0; }
+
+extern "C" int64_t fft_plan_workspace_bytes(fft_plan_t p) { return p ? p->ws_bytes : 0; }
+
+extern "C" int fft_version(void) { return 100; }

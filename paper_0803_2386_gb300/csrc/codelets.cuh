@@ -1,0 +1,190 @@
+// codelets.cuh -- register-resident radix-2^k DFT codelets.
+//
+// A codelet of size E = 2^k performs k radix-2 stages on E values held in
+// registers: the innermost level of the memory hierarchy, where the paper's
+// "block of length c" (Ch.3) is the register file of one thread.  Each
+// codelet splits its input index top digit first, n = (E/4)*n0 + n1, does
+// the small DFTs over n0, multiplies by w_E^(n1*k0) and finishes with DFTs
+// over n1 (the same recursion the passes use at the HBM and shared-memory
+// levels).  Outputs come back in natural order; the digit reversal inside a
+// codelet costs nothing because it is a renaming of registers.
+//
+// DIR is the exponent sign s: w_E = exp(s * 2*pi*i / E).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace moafft {
+
+template <typename T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+
+template <typename V>
+__host__ __device__ __forceinline__ V c_add(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V>
+__host__ __device__ __forceinline__ V c_sub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+// a * w (w a table weight), four real products
+template <typename V>
+__host__ __device__ __forceinline__ V c_mul(V a, V w)
+{
+    V r;
+    r.x = a.x * w.x - a.y * w.y;
+    r.y = a.x * w.y + a.y * w.x;
+    return r;
+}
+
+// a * conj(w)
+template <typename V>
+__host__ __device__ __forceinline__ V c_mulc(V a, V w)
+{
+    V r;
+    r.x = a.x * w.x + a.y * w.y;
+    r.y = a.y * w.x - a.x * w.y;
+    return r;
+}
+
+// multiply by a forward-table weight w = exp(-i theta) in direction DIR:
+// DIR = -1 uses w, DIR = +1 uses conj(w).
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ V c_tw(V a, V w)
+{
+    if constexpr (DIR < 0) return c_mul(a, w);
+    else return c_mulc(a, w);
+}
+
+// multiply by s*i  (w_4 in direction s)
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ V c_rot(V a)
+{
+    V r;
+    if constexpr (DIR < 0) { r.x = a.y; r.y = -a.x; }
+    else { r.x = -a.y; r.y = a.x; }
+    return r;
+}
+
+// multiply by w_16^J in direction DIR, J in {0..9}; constants are
+// cos/sin of multiples of pi/8.
+template <int DIR, int J, typename V>
+__host__ __device__ __forceinline__ V c_w16(V a)
+{
+    using T = decltype(a.x);
+    constexpr T C1 = (T)0.92387953251128675613;  // cos(pi/8)
+    constexpr T S1 = (T)0.38268343236508977173;  // sin(pi/8)
+    constexpr T H = (T)0.70710678118654752440;   // sqrt(2)/2
+    constexpr T s = (T)DIR;
+    if constexpr (J == 0) {
+        return a;
+    } else if constexpr (J == 4) {
+        return c_rot<DIR>(a);
+    } else if constexpr (J == 2) {  // H*(1 + s i)
+        V r;
+        r.x = H * (a.x - s * a.y);
+        r.y = H * (a.y + s * a.x);
+        return r;
+    } else if constexpr (J == 6) {  // H*(-1 + s i)
+        V r;
+        r.x = -H * (a.x + s * a.y);
+        r.y = H * (s * a.x - a.y);
+        return r;
+    } else {
+        static_assert(J == 1 || J == 3 || J == 9, "w16 exponent");
+        constexpr T cr = J == 1 ? C1 : (J == 3 ? S1 : -C1);
+        constexpr T ci = J == 1 ? s * S1 : (J == 3 ? s * C1 : -s * S1);
+        V r;
+        r.x = a.x * cr - a.y * ci;
+        r.y = a.x * ci + a.y * cr;
+        return r;
+    }
+}
+
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ void dft2(V &a, V &b)
+{
+    V t = a;
+    a = c_add(t, b);
+    b = c_sub(t, b);
+}
+
+// 4-point DFT of (v0, v1, v2, v3), natural order in and out
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ void dft4(V &v0, V &v1, V &v2, V &v3)
+{
+    V a = c_add(v0, v2), b = c_sub(v0, v2);
+    V c = c_add(v1, v3), d = c_rot<DIR>(c_sub(v1, v3));
+    v0 = c_add(a, c);
+    v2 = c_sub(a, c);
+    v1 = c_add(b, d);
+    v3 = c_sub(b, d);
+}
+
+// 8-point DFT: n = 4*n0 + n1, k = k0 + 2*k1
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ void dft8(V *v)
+{
+    using T = decltype(v[0].x);
+    constexpr T H = (T)0.70710678118654752440;
+    constexpr T s = (T)DIR;
+#pragma unroll
+    for (int n1 = 0; n1 < 4; n1++) dft2<DIR>(v[n1], v[n1 + 4]);
+    // w_8^n1 on the k0 = 1 half
+    {
+        V a = v[5];  // w_8 = H*(1 + s i)
+        v[5].x = H * (a.x - s * a.y);
+        v[5].y = H * (a.y + s * a.x);
+        v[6] = c_rot<DIR>(v[6]);
+        a = v[7];  // w_8^3 = H*(-1 + s i)
+        v[7].x = -H * (a.x + s * a.y);
+        v[7].y = H * (s * a.x - a.y);
+    }
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+    dft4<DIR>(v[4], v[5], v[6], v[7]);
+    V o[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+        o[2 * k1] = v[k1];
+        o[2 * k1 + 1] = v[4 + k1];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = o[k];
+}
+
+// 16-point DFT: n = 4*n0 + n1, k = k0 + 4*k1
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ void dft16(V *v)
+{
+#pragma unroll
+    for (int n1 = 0; n1 < 4; n1++) dft4<DIR>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]);
+    // now v[n1 + 4*k0] = Y[n1][k0]; twiddle by w_16^(n1*k0)
+    v[5] = c_w16<DIR, 1>(v[5]);
+    v[6] = c_w16<DIR, 2>(v[6]);
+    v[7] = c_w16<DIR, 3>(v[7]);
+    v[9] = c_w16<DIR, 2>(v[9]);
+    v[10] = c_w16<DIR, 4>(v[10]);
+    v[11] = c_w16<DIR, 6>(v[11]);
+    v[13] = c_w16<DIR, 3>(v[13]);
+    v[14] = c_w16<DIR, 6>(v[14]);
+    v[15] = c_w16<DIR, 9>(v[15]);
+#pragma unroll
+    for (int k0 = 0; k0 < 4; k0++) dft4<DIR>(v[4 * k0], v[4 * k0 + 1], v[4 * k0 + 2], v[4 * k0 + 3]);
+    // v[4*k0 + k1] = X[k0 + 4*k1]
+    V o[16];
+#pragma unroll
+    for (int k0 = 0; k0 < 4; k0++)
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) o[k0 + 4 * k1] = v[4 * k0 + k1];
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = o[k];
+}
+
+template <int DIR, int LE, typename V>
+__host__ __device__ __forceinline__ void dft_codelet(V *v)
+{
+    if constexpr (LE == 1) dft2<DIR>(v[0], v[1]);
+    else if constexpr (LE == 2) dft4<DIR>(v[0], v[1], v[2], v[3]);
+    else if constexpr (LE == 3) dft8<DIR>(v);
+    else if constexpr (LE == 4) dft16<DIR>(v);
+}
+
+}  // namespace moafft

@@ -1,0 +1,80 @@
+// internal.h -- host-side structures shared by the C-ABI layer and the
+// kernel launchers.  Not part of the public ABI (include/moafft.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "moafft.h"
+
+namespace moafft {
+
+constexpr int kMaxPasses = 8;  // log2 n <= 40 with tiles of >= 2^5
+constexpr int kMaxSub = 4;     // register sub-passes per tile (4 x radix-16)
+
+// One HBM pass of the dimension-lifted signal.  The transform of length n
+// is viewed as an A x R x B array (n = A*R*B); the pass performs, for every
+// (a, b), an R-point DFT over the middle axis (a group of log2 R radix-2
+// stages, Ch.3 "Re-Ordering of Butterfly Operations"), multiplies by the
+// weights w_{R*B}^{b*k} that the following groups need (Sec. "General Weight
+// Sub-Matrices": the tracked weights w_L^(sigma + j c^l)), and writes the
+// result in the layout the next pass reads (the reshape-transpose becomes an
+// addressing rule).  The last pass writes through the final transpose
+// (Eq. xihyper) into the caller's buffer.
+struct PassDesc {
+    int log_r = 0;               // log2 R
+    int width = 1;               // columns (rows in the last pass) per CTA
+    int nsub = 0;                // register-level sub-passes inside the tile
+    int sub_log[kMaxSub] = {0};  // log2 radix of each sub-pass, top digit first
+    int64_t A = 1, B = 1;        // n = A * R * B
+    int tw_lo_bits = 0;          // 0: direct pass-twiddle table, else two-level
+    int64_t tw_m = 1;            // M = R*B: pass twiddles are w_M^e
+    size_t tw_tile_off = 0;      // element offsets into the plan's twiddle arena
+    size_t tw_pass_off = 0;
+    size_t tw_hi_off = 0;
+};
+
+struct Schedule {
+    int64_t n = 1;
+    int t = 0;
+    int npass = 0;
+    PassDesc pass[kMaxPasses];
+};
+
+// Parameters of one pass launch (passed by value to the kernel).
+struct PassArgs {
+    const void *in;
+    void *out;
+    int64_t n;        // transform length
+    int64_t count;    // transforms covered by this launch
+    int log_r;
+    int width;
+    int nsub;
+    int sub_log[kMaxSub];
+    int64_t A, B;
+    int is_last;
+    int npass;                  // passes of the whole schedule
+    int pass_log[kMaxPasses];   // their log2 radices (for the final transpose)
+    const void *tw_tile;        // w_R^e, e < R
+    const void *tw_pass;        // w_M^e (direct) or w_M^e, e < 2^lo_bits (two-level)
+    const void *tw_hi;          // w_M^(e << lo_bits) (two-level)
+    int tw_lo_bits;
+    double scale;               // applied in the last pass (1 or 1/n)
+};
+
+// kernel launchers (kernels_f32.cu / kernels_f64.cu)
+cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);
+cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);
+
+// twiddle generation (twiddle.cu): dst[j] = exp(-2*pi*i * j*stride / m),
+// j < count, computed in FP64 with sincospi; f32 variant rounds once.
+cudaError_t launch_twiddle_f64(double *dst, int64_t count, int64_t m, int64_t stride,
+                               cudaStream_t s);
+cudaError_t launch_twiddle_f32(float *dst, int64_t count, int64_t m, int64_t stride,
+                               cudaStream_t s);
+
+// threads per CTA for a pass
+int pass_threads(const PassArgs &a);
+size_t pass_smem_bytes(const PassArgs &a, size_t elem_bytes);
+
+}  // namespace moafft

@@ -1,0 +1,63 @@
+// twiddle.cu -- device generation of the weight tables.
+//
+// The weights w_M^e = exp(-2*pi*i*e/M) are produced on the GPU in FP64 with
+// sincospi (the argument 2*e/M is exact for M a power of two), so the tables
+// carry one rounding of the exact values.  The FP32 tables are the FP64
+// values rounded once more.  (fftpsirad2 recomputes its weights per stage
+// with EXP, Fig. fftpsirad2; here each table is built once per plan.)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace moafft {
+
+__global__ void twiddle_f64_kernel(double2 *dst, int64_t count, int64_t m, int64_t stride)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (j * stride) % m;
+        double s, c;
+        sincospi(2.0 * (double)e / (double)m, &s, &c);
+        dst[j] = make_double2(c, -s);
+    }
+}
+
+__global__ void twiddle_f32_kernel(float2 *dst, int64_t count, int64_t m, int64_t stride)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (j * stride) % m;
+        double s, c;
+        sincospi(2.0 * (double)e / (double)m, &s, &c);
+        dst[j] = make_float2((float)c, (float)-s);
+    }
+}
+
+static int grid_for(int64_t count)
+{
+    int64_t g = (count + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_twiddle_f64(double *dst, int64_t count, int64_t m, int64_t stride,
+                               cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    twiddle_f64_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<double2 *>(dst), count,
+                                                        m, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle_f32(float *dst, int64_t count, int64_t m, int64_t stride,
+                               cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    twiddle_f32_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<float2 *>(dst), count,
+                                                        m, stride);
+    return cudaGetLastError();
+}
+
+}  // namespace moafft

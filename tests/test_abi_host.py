@@ -1,0 +1,121 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol
+include/moafft.h declares, and rejects bad arguments before touching a GPU.
+No compute call runs here."""
+import json
+import os
+import re
+
+import pytest
+
+import paper_0803_2386_gb300 as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    M.build()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(fft_[a-z_0-9]+)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_what_binding_lists():
+    assert set(declared_functions()) == set(M.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = M.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_version_and_no_error():
+    assert M.fft_version() >= 100
+
+
+@pytest.mark.parametrize("n,bad", [(0, M.FFT_ERR_ARG), (-4, M.FFT_ERR_ARG), (12, M.FFT_ERR_NOT_POW2),
+                                   (1000, M.FFT_ERR_NOT_POW2), (1 << 31, M.FFT_ERR_UNSUPPORTED)])
+def test_plan_rejects_bad_length(n, bad):
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan(n, 1, M.FFT_C128, M.FFT_FORWARD)
+    assert e.value.status == bad
+    assert M.fft_last_error()
+
+
+def test_plan_rejects_bad_batch_dtype_dir_form():
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan(16, 0)
+    assert e.value.status == M.FFT_ERR_ARG
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan(16, 1, 7)
+    assert e.value.status == M.FFT_ERR_DTYPE
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan(16, 1, M.FFT_C64, 0)
+    assert e.value.status == M.FFT_ERR_DTYPE
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan_ex(16, 1, M.FFT_C64, M.FFT_FORWARD, 9)
+    assert e.value.status == M.FFT_ERR_ARG
+
+
+def test_bad_schedules():
+    for text in ["3,3", "x", "5,5,", "5@3,5", "10@0", "4,4,4,4,4,4,4,4,4"]:
+        with pytest.raises(M.MoaFFTError) as e:
+            M.fft_describe_schedule(1 << 10, M.FFT_C128, M.FFT_FORM_PLAIN, text)
+        assert e.value.status == M.FFT_ERR_ARG, text
+
+
+def test_null_handles():
+    L = M.lib()
+    assert L.fft_destroy(None) == 0
+    assert L.fft_exec(None, None, None, None) == M.FFT_ERR_ARG
+    assert L.fft_exec_adjoint(None, None, None, None) == M.FFT_ERR_ARG
+    assert L.fft_plan(None, 16, 1, 0, -1) == M.FFT_ERR_ARG
+    assert L.fft_plan_launches(None) == 0
+
+
+@pytest.mark.parametrize("t", range(0, 25))
+@pytest.mark.parametrize("dt", [M.FFT_C64, M.FFT_C128])
+def test_default_schedule_covers_all_stages(t, dt):
+    """The passes' radices add up to log2 n (every radix-2 stage once, Fig.
+    vanloan_fft) and each pass lifts n to A x R x B consistently."""
+    n = 1 << t
+    s = json.loads(M.fft_describe_schedule(n, dt))
+    assert s["n"] == n
+    A = 1
+    total = 0
+    for i, p in enumerate(s["passes"]):
+        R = 1 << p["log_r"]
+        assert p["A"] == A and p["A"] * R * p["B"] == n
+        assert sum(p["sub_log"]) == p["log_r"] and all(1 <= x <= 4 for x in p["sub_log"])
+        assert R * p["width"] <= (4096 if dt == M.FFT_C128 else 8192) * 2
+        if i < len(s["passes"]) - 1:
+            assert p["B"] % p["width"] == 0 and p["tw_m"] == R * p["B"]
+        A *= R
+        total += p["log_r"]
+    assert total == t
+    assert s["passes"][-1]["B"] == 1
+
+
+def test_explicit_schedule_parse():
+    s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "4@8,4,4"))
+    assert [p["log_r"] for p in s["passes"]] == [4, 4, 4]
+    assert s["passes"][0]["width"] == 8
+    assert [p["B"] for p in s["passes"]] == [256, 16, 1]
+
+
+def test_allocator_hook_arguments():
+    with pytest.raises(M.MoaFFTError):
+        M.lib().fft_set_allocator(M.ALLOC_FN(lambda n, c: 0), M.FREE_FN(), None) and None
+        _ = M._check(M.lib().fft_set_allocator(M.ALLOC_FN(lambda n, c: 0), M.FREE_FN(), None))
+    M.fft_set_allocator(None, None)
