@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the batched MoA radix-2 FFT on GB300.
+
+Workload (one "step"): the complex128 plain-method configuration at scale,
+n = 2^20 with batch 64 (n * batch = 2^26 elements, 1 GiB per buffer), one
+forward and one inverse transform of the whole batch.  Inputs are seeded
+synthetic data (uniform [-1, 1] real and imaginary parts) resident in HBM;
+every buffer is larger than L2 (129 MB), so no flush is needed.
+
+Printed: one JSON line (rank 0) with the metric in GFLOP/s = 5 n log2 n per
+transform, the end-to-end figure through host buffers (fft_exec_host), the
+roofline of the dominant kernel measured live with CUDA events, the SM
+clocks sampled during the timed region, and the FP64 CPU oracle timed on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moafft|reference]
+Under torchrun each rank runs the same per-GPU workload on its own GPU
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched FFT GFLOP/s (5N·log2N) & %HBM roofline, FP64 plain vs FP32/TC at rel err"
+UNIT = "GFLOP/s"
+# FP64 issue peak of GB300: 152 SMs x 2 DFMA per SM per clock x 2 flop x
+# 2.07 GHz maximum SM clock (the throughput probe measured 2.0 DFMA per SM per
+# clock); the recipe's nominal FP64 figure is 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="moafft", choices=["moafft", "reference"])
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=0, help="override the batch (small profiling cases)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
+    return ap.parse_args()
+
+
+def workload(log2n: int, batch: int = 0):
+    n = 1 << log2n
+    return n, (batch if batch > 0 else (1 << 26) // n)
+
+
+def config(n, batch, world):
+    return {"workload": f"c128 plain radix-2 FFT, n=2^{int(math.log2(n))}, batch {batch} "
+                        f"(n*batch=2^{int(math.log2(n * batch))}, {n * batch * 16 / 2**30:g} GiB per "
+                        f"buffer), forward+inverse per step",
+            "n": n, "batch_per_gpu": batch, "global_batch": batch * world,
+            "dtype": "complex128", "parallelism": f"batch-shard x{world}",
+            "l2": "inputs larger than L2 (1 GiB per buffer > 129 MB); no flush"}
+
+
+def flops_per_step(n, batch):
+    return 2 * 5.0 * n * math.log2(n) * batch  # forward + inverse
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi every 200 ms while running (the recipe's clocks line)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def source_hash() -> str:
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0803_2386_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, workload_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get(f"{kernel}|{workload_key}")
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def cpu_baseline(n: int, batch: int, target_s: float = 12.0):
+    """Time the FP64 oracle (as it stands) on the host cores on a bounded
+    sample of the workload: forward + inverse of S transforms."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    cores = os.cpu_count() or 1
+    x1 = W.uniform_complex(n, 1, seed=0)
+    t0 = time.perf_counter()
+    O.fft(x1, "forward", c=1024, threads=1)
+    t1 = max(time.perf_counter() - t0, 1e-3)
+    s = int(min(batch, max(cores, math.ceil(target_s / (2 * t1)))))
+    s = max(1, min(batch, (s // cores) * cores if s >= cores else s))
+    threads = min(cores, s)
+    x = W.uniform_complex(n, s, seed=0)
+    t0 = time.perf_counter()
+    X = O.fft(x, "forward", c=1024, threads=threads)
+    O.fft(X, "inverse", c=1024, threads=threads)
+    dt = time.perf_counter() - t0
+    gflops = 2 * 5.0 * n * math.log2(n) * s / dt / 1e9
+    return {"value": round(gflops, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{s} of the {batch} transforms of n=2^{int(math.log2(n))}, forward+inverse, "
+                      f"{threads} threads, {dt:.2f} s wall"}
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    import workloads as W
+    n, batch = workload(args.log2n, args.batch)
+    cores = os.cpu_count() or 1
+    s = min(batch, cores)
+    x = W.uniform_complex(n, s, seed=0)
+
+    def step():
+        X = O.fft(x, "forward", c=1024, threads=s)
+        O.fft(X, "inverse", c=1024, threads=s)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = 2 * 5.0 * n * math.log2(n) * s / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded uniform[-1,1])",
+            "config": config(n, batch, world),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": s, "kind": "oracle",
+                             "sample": f"each step: {s} of the {batch} transforms, forward+inverse, "
+                                       f"{s} threads (FP64 CPU oracle, plain C)"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ moafft
+
+def run_moafft(args):
+    import torch
+    import paper_0803_2386_gb300 as M
+    import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    M.lib()  # no fallback: fails loudly if the library is missing
+
+    n, batch = workload(args.log2n, args.batch)
+    x = torch.from_numpy(W.uniform_complex(n, batch, seed=rank)).to(dev)
+    X = torch.empty_like(x)
+    y = torch.empty_like(x)
+    fwd = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD)
+    inv = M.Plan(n, batch, M.FFT_C128, M.FFT_INVERSE)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fwd.exec(x, X, stream)
+        inv.exec(X, y, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    # round-trip check on the warm data (cheap, on device)
+    rt = (torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x)).item()
+
+    fwd_desc = json.loads(fwd.describe())
+    M.fft_plan_profile(fwd.handle, True)
+    M.fft_plan_profile(inv.handle, True)
+    M.fft_plan_pass_times(fwd.handle)
+    M.fft_plan_pass_times(inv.handle)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = t.item()
+    ms_step = t_ms / args.steps
+    value = flops_per_step(n, batch) * world / (ms_step * 1e-3) / 1e9
+    launches = args.steps * (fwd.launches + inv.launches)
+
+    # dominant kernel: the pass with the largest accumulated time
+    ft = M.fft_plan_pass_times(fwd.handle)
+    it = M.fft_plan_pass_times(inv.handle)
+    M.fft_plan_profile(fwd.handle, False)
+    M.fft_plan_profile(inv.handle, False)
+    passes = fwd_desc["schedule"]["passes"]
+    per_pass = []
+    for i, p in enumerate(passes):
+        ms = ft[i][0] + it[i][0]
+        cnt = ft[i][1] + it[i][1]
+        per_pass.append((ms, cnt, i))
+    ms_tot, cnt, dom = max(per_pass)
+    chunk = fwd_desc["chunk"]
+    log_r = passes[dom]["log_r"]
+    avg_ms = ms_tot / max(cnt, 1)
+    flops_launch = 5.0 * chunk * n * log_r
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    kname = f"pass_kernel<double> pass {dom} (log2 R = {log_r})"
+    wkey = f"c128 n=2^{args.log2n}"
+    traffic = recorded_traffic(f"pass{dom}", wkey)
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "kernel": kname, "avg_launch_ms": round(avg_ms, 4),
+                "algorithmic_per_launch": f"5 flop x {chunk} transforms x 2^{args.log2n} x {log_r} stages",
+                "peak_source": "FP64 issue peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "hbm_gbs_algorithmic_step": round(2 * 2 * n * batch * 16 / (ms_step * 1e-3) / 1e9, 1),
+                "hbm_frac_of_measured": None}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        roofline["hbm_frac_of_measured"] = round(roofline["hbm_gbs_algorithmic_step"] / peaks["hbm_gbs"], 4)
+    except (OSError, ValueError, KeyError):
+        pass
+
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, world, args)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded uniform[-1,1], seed = rank)",
+                "config": config(n, batch, world), "gpu_launches": launches,
+                "roundtrip_rel_err": rt, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(n, batch)
+        print(json.dumps(line), flush=True)
+
+    for t in [int(v) for v in args.sweep.split(",") if v.strip()]:
+        sweep_line(M, torch, dev, stream, t, args)
+
+    fwd.close()
+    inv.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, world, args):
+    """End to end through host buffers (pinned): H2D and D2H inside the timing."""
+    xh = x.cpu().pin_memory()
+    Xh = torch.empty_like(xh).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+
+    def e2e_step():
+        M.fft_exec_host(fwd.handle, xh, Xh, stream)
+        M.fft_exec_host(inv.handle, Xh, yh, stream)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    rt_host = float((torch.linalg.vector_norm(yh - xh) / torch.linalg.vector_norm(xh)).item())
+    bytes_buf = n * batch * 16
+    e2e = {"value": round(flops_per_step(n, batch) * world / e2e_s / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * bytes_buf, "d2h_bytes_per_step": 2 * bytes_buf,
+           "ms_per_step": round(e2e_s * 1e3, 3), "api": "fft_exec_host (pinned host buffers)",
+           "roundtrip_rel_err": rt_host}
+    return e2e
+
+
+def sweep_line(M, torch, dev, stream, log2n, args):
+    n, batch = workload(log2n)
+    x = torch.rand(batch, n, dtype=torch.complex128, device=dev) * 2 - (1 + 1j)
+    X = torch.empty_like(x)
+    y = torch.empty_like(x)
+    fwd = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD)
+    inv = M.Plan(n, batch, M.FFT_C128, M.FFT_INVERSE)
+    for _ in range(2):
+        fwd.exec(x, X, stream)
+        inv.exec(X, y, stream)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    k = max(1, args.steps // 2)
+    for _ in range(k):
+        fwd.exec(x, X, stream)
+        inv.exec(X, y, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / k
+    print(json.dumps({"sweep": True, "n": n, "batch": batch, "ms_per_step": round(ms, 4),
+                      "gflops": round(flops_per_step(n, batch) / (ms * 1e-3) / 1e9, 2)}),
+          file=sys.stderr, flush=True)
+    fwd.close()
+    inv.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_moafft(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

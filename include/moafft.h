@@ -112,6 +112,18 @@ int fft_exec(fft_plan_t p, const void *in, void *out, void *cuda_stream);
  * conjugate transpose of the butterfly block). */
 int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream);
 
+/* As fft_exec, for HOST buffers: `in` and `out` are host pointers (pinned
+ * memory gives full copy speed; pageable memory works but copies are
+ * staged by the driver).  The batch is streamed through device staging
+ * buffers the plan allocates on first use (two slots of up to 64 MiB each):
+ * host-to-device copy, transform and device-to-host copy of consecutive
+ * slices overlap on the plan's own copy streams.  The call returns after
+ * enqueueing; `cuda_stream` waits for the last copy, so synchronising it
+ * makes `out` valid.  in == out is allowed.  The paper times whole
+ * executables including data movement (Ch.1 "Experiments"); this is that
+ * end-to-end path. */
+int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream);
+
 /* Release everything the plan owns.  NULL is a no-op.  Synchronises the
  * device before freeing. */
 int fft_destroy(fft_plan_t p);
@@ -136,6 +148,15 @@ int64_t fft_plan_launches(fft_plan_t p);
 
 /* Bytes of device workspace the plan holds (twiddle tables excluded). */
 int64_t fft_plan_workspace_bytes(fft_plan_t p);
+
+/* Kernel timing: with enable != 0, every kernel launch of fft_exec /
+ * fft_exec_adjoint on this plan is bracketed by CUDA events on its stream,
+ * and the per-pass totals accumulate until read.  fft_plan_pass_times
+ * synchronises the recorded events, writes for each pass i < max_passes the
+ * total milliseconds (ms[i]) and launch count (launches[i]), resets the
+ * totals and returns the number of passes.  Disabled by default. */
+int fft_plan_profile(fft_plan_t p, int enable);
+int fft_plan_pass_times(fft_plan_t p, double *ms, int64_t *launches, int max_passes);
 
 /* Replace the device allocator used by subsequent fft_plan* calls.  alloc
  * returns a device pointer of at least `bytes` or NULL; release frees it.

@@ -40,7 +40,7 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
 
 # every symbol include/moafft.h declares
 EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_exec", "fft_exec_adjoint",
-           "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
+           "fft_exec_host", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
            "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_version"]
 
 _LIB = None
@@ -77,6 +77,10 @@ def lib():
             "fft_plan_many": (i32, [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i32, i32]),
             "fft_exec": (i32, [vp, vp, vp, vp]),
             "fft_exec_adjoint": (i32, [vp, vp, vp, vp]),
+            "fft_exec_host": (i32, [vp, vp, vp, vp]),
+            "fft_plan_profile": (i32, [vp, i32]),
+            "fft_plan_pass_times": (i32, [vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(i64), i32]),
             "fft_destroy": (i32, [vp]),
             "fft_last_error": (ctypes.c_char_p, []),
             "fft_describe_schedule": (i32, [i64, i32, i32, ctypes.c_char_p, ctypes.c_char_p, i64]),
@@ -159,6 +163,31 @@ def fft_exec(plan: int, inp, out, stream=None):
 
 def fft_exec_adjoint(plan: int, inp, out, stream=None):
     _check(lib().fft_exec_adjoint(plan, _ptr(inp), _ptr(out), _stream(stream, inp, out)))
+
+
+def fft_exec_host(plan: int, inp, out, stream=None):
+    """Host buffers (numpy arrays, pinned torch CPU tensors or raw ints)."""
+    def hp(x):
+        if isinstance(x, int):
+            return x
+        if hasattr(x, "ctypes"):
+            return x.ctypes.data
+        return int(x.data_ptr())
+    _check(lib().fft_exec_host(plan, hp(inp), hp(out), _stream(stream)))
+
+
+def fft_plan_profile(plan: int, enable: bool = True):
+    _check(lib().fft_plan_profile(plan, 1 if enable else 0))
+
+
+def fft_plan_pass_times(plan: int, max_passes: int = 8):
+    """[(total_ms, launches) per pass] since the last read (resets them)."""
+    ms = (ctypes.c_double * max_passes)()
+    cnt = (ctypes.c_int64 * max_passes)()
+    k = lib().fft_plan_pass_times(plan, ms, cnt, max_passes)
+    if k < 0:
+        _check(k)
+    return [(ms[i], cnt[i]) for i in range(k)]
 
 
 def fft_destroy(plan: int):

@@ -264,7 +264,36 @@ struct fft_plan_s {
     DevBuf ws;          // inter-pass workspace
     int64_t ws_bytes = 0;
     int device = 0;
+    // kernel timing (fft_plan_profile)
+    bool profile = false;
+    struct Rec {
+        int pass;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_free;
+    // host-buffer pipeline (fft_exec_host), created on first use
+    DevBuf stage_in[2], stage_out[2];
+    int64_t stage_tr = 0;  // transforms per staging slot
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_d2h[2] = {nullptr, nullptr};
 };
+
+static cudaEvent_t take_event(fft_plan_s *p)
+{
+    if (!p->ev_free.empty()) {
+        cudaEvent_t e = p->ev_free.back();
+        p->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
 
 namespace moafft {
 int pass_threads(const PassArgs &a)
@@ -424,6 +453,20 @@ extern "C" int fft_destroy(fft_plan_t p)
     cudaError_t e = cudaDeviceSynchronize();
     dev_free(p->ws);
     dev_free(p->tw);
+    for (int k = 0; k < 2; k++) {
+        dev_free(p->stage_in[k]);
+        dev_free(p->stage_out[k]);
+        if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
+        if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+        if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
+    }
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+    for (auto &r : p->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto ev : p->ev_free) cudaEventDestroy(ev);
     delete p;
     if (e != cudaSuccess) return fail_cuda(e, "fft_destroy (sync)");
     return FFT_OK;
@@ -446,41 +489,28 @@ static int check_device_ptr(const void *ptr, size_t align, const char *what)
     return FFT_OK;
 }
 
-static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoint)
+// Transforms [b0, b0 + cnt) of the batch, device buffers already checked.
+// in/out point at transform b0.
+static int exec_range(fft_plan_t p, const void *in, void *out, int64_t cnt, int sign, double scale,
+                      cudaStream_t s)
 {
-    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
     size_t eb = elem_bytes(p->dt);
-    int st = check_device_ptr(in, eb, "in");
-    if (st != FFT_OK) return st;
-    st = check_device_ptr(out, eb, "out");
-    if (st != FFT_OK) return st;
-    const size_t bytes = (size_t)p->n * (size_t)p->batch * eb;
-    uintptr_t a0 = (uintptr_t)in, a1 = a0 + bytes, b0 = (uintptr_t)out, b1 = b0 + bytes;
-    if (in != out && a0 < b1 && b0 < a1)
-        return fail(FFT_ERR_ALIAS, "in and out overlap without being identical");
-
-    // direction and scaling: forward s=-1 unscaled, inverse s=+1 x 1/n;
-    // adjoint swaps the sign and keeps the scaling.
-    int sign = (int)p->dir;
-    if (adjoint) sign = -sign;
-    double scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
-
-    cudaStream_t s = (cudaStream_t)stream;
     const Schedule &S = p->sched;
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.n = p->n;
     a.npass = S.npass;
     for (int i = 0; i < S.npass; i++) a.pass_log[i] = S.pass[i].log_r;
-    for (int64_t c0 = 0; c0 < p->batch; c0 += p->chunk) {
-        int64_t cnt = std::min(p->chunk, p->batch - c0);
+    const int64_t chunk = S.npass > 1 ? p->chunk : cnt;
+    for (int64_t c0 = 0; c0 < cnt; c0 += chunk) {
+        int64_t c = std::min(chunk, cnt - c0);
         const char *src = (const char *)in + (size_t)c0 * p->n * eb;
         char *dst = (char *)out + (size_t)c0 * p->n * eb;
         for (int i = 0; i < S.npass; i++) {
             const PassDesc &d = S.pass[i];
             a.in = (i == 0) ? (const void *)src : p->ws.ptr;
             a.out = (i == S.npass - 1) ? (void *)dst : p->ws.ptr;
-            a.count = cnt;
+            a.count = c;
             a.log_r = d.log_r;
             a.width = d.width;
             a.nsub = d.nsub;
@@ -493,9 +523,132 @@ static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoi
             a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
             a.tw_lo_bits = d.tw_lo_bits;
             a.scale = a.is_last ? scale : 1.0;
+            fft_plan_s::Rec rec{i, nullptr, nullptr};
+            if (p->profile) {
+                rec.a = take_event(p);
+                rec.b = take_event(p);
+                if (rec.a) cudaEventRecord(rec.a, s);
+            }
             cudaError_t e = p->dt == FFT_C128 ? launch_pass_f64(a, sign, s) : launch_pass_f32(a, sign, s);
             if (e != cudaSuccess) return fail_cuda(e, "pass launch");
+            if (p->profile && rec.a && rec.b) {
+                cudaEventRecord(rec.b, s);
+                p->recs.push_back(rec);
+            }
         }
+    }
+    return FFT_OK;
+}
+
+static void direction_of(fft_plan_t p, bool adjoint, int *sign, double *scale)
+{
+    // forward s=-1 unscaled, inverse s=+1 x 1/n; the adjoint swaps the sign
+    // and keeps the scaling.
+    *sign = (int)p->dir;
+    if (adjoint) *sign = -*sign;
+    *scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
+}
+
+static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoint)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    size_t eb = elem_bytes(p->dt);
+    int st = check_device_ptr(in, eb, "in");
+    if (st != FFT_OK) return st;
+    st = check_device_ptr(out, eb, "out");
+    if (st != FFT_OK) return st;
+    const size_t bytes = (size_t)p->n * (size_t)p->batch * eb;
+    uintptr_t a0 = (uintptr_t)in, a1 = a0 + bytes, b0 = (uintptr_t)out, b1 = b0 + bytes;
+    if (in != out && a0 < b1 && b0 < a1)
+        return fail(FFT_ERR_ALIAS, "in and out overlap without being identical");
+    int sign;
+    double scale;
+    direction_of(p, adjoint, &sign, &scale);
+    return exec_range(p, in, out, p->batch, sign, scale, (cudaStream_t)stream);
+}
+
+static int check_host_ptr(const void *ptr, const char *what)
+{
+    if (!ptr) return fail(FFT_ERR_ARG, "%s is NULL", what);
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_OK;  // unknown to CUDA: ordinary pageable host memory
+    }
+    if (attr.type == cudaMemoryTypeDevice)
+        return fail(FFT_ERR_ARG, "%s is device memory; fft_exec_host takes host buffers", what);
+    return FFT_OK;
+}
+
+static int setup_staging(fft_plan_t p)
+{
+    if (p->stage_tr > 0) return FFT_OK;
+    size_t eb = elem_bytes(p->dt);
+    const int64_t slot_bytes = (int64_t)64 << 20;
+    int64_t tr = std::max<int64_t>(1, slot_bytes / (p->n * (int64_t)eb));
+    tr = std::min(tr, p->batch);
+    size_t bytes = (size_t)tr * p->n * eb;
+    for (int k = 0; k < 2; k++) {
+        int st = dev_alloc(p->stage_in[k], bytes, "host staging (in)");
+        if (st == FFT_OK) st = dev_alloc(p->stage_out[k], bytes, "host staging (out)");
+        if (st != FFT_OK) return st;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaEventCreateWithFlags(&p->ev_h2d[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_d2h[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "staging streams/events");
+    p->stage_tr = tr;
+    return FFT_OK;
+}
+
+// Slice i uses slot i % 2: H2D on s_h2d, transform on the caller's stream,
+// D2H on s_d2h; events order the reuse of each slot.
+static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    int st = check_host_ptr(in, "in");
+    if (st == FFT_OK) st = check_host_ptr(out, "out");
+    if (st == FFT_OK) st = setup_staging(p);
+    if (st != FFT_OK) return st;
+    int sign;
+    double scale;
+    direction_of(p, false, &sign, &scale);
+    size_t eb = elem_bytes(p->dt);
+    cudaStream_t cs = (cudaStream_t)stream;
+    bool used[2] = {false, false};
+    for (int64_t b0 = 0, i = 0; b0 < p->batch; b0 += p->stage_tr, i++) {
+        int k = (int)(i & 1);
+        int64_t cnt = std::min(p->stage_tr, p->batch - b0);
+        size_t off = (size_t)b0 * p->n * eb, bytes = (size_t)cnt * p->n * eb;
+        cudaError_t e = cudaSuccess;
+        if (used[k]) e = cudaStreamWaitEvent(p->s_h2d, p->ev_comp[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->stage_in[k].ptr, (const char *)in + off, bytes, cudaMemcpyHostToDevice,
+                                p->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_h2d[k], p->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->ev_h2d[k], 0);
+        if (e == cudaSuccess && used[k]) e = cudaStreamWaitEvent(cs, p->ev_d2h[k], 0);
+        if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (copy in)");
+        st = exec_range(p, p->stage_in[k].ptr, p->stage_out[k].ptr, cnt, sign, scale, cs);
+        if (st != FFT_OK) return st;
+        e = cudaEventRecord(p->ev_comp[k], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char *)out + off, p->stage_out[k].ptr, bytes, cudaMemcpyDeviceToHost,
+                                p->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_d2h[k], p->s_d2h);
+        if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (copy out)");
+        used[k] = true;
+    }
+    for (int k = 0; k < 2; k++) {
+        if (!used[k]) continue;
+        cudaError_t e = cudaStreamWaitEvent(cs, p->ev_d2h[k], 0);
+        if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (join)");
     }
     return FFT_OK;
 }
@@ -508,6 +661,42 @@ extern "C" int fft_exec(fft_plan_t p, const void *in, void *out, void *cuda_stre
 extern "C" int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream)
 {
     return run(p, in, out, cuda_stream, true);
+}
+
+extern "C" int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream)
+{
+    return run_host(p, in, out, cuda_stream);
+}
+
+extern "C" int fft_plan_profile(fft_plan_t p, int enable)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    p->profile = enable != 0;
+    return FFT_OK;
+}
+
+extern "C" int fft_plan_pass_times(fft_plan_t p, double *ms, int64_t *launches, int max_passes)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    if ((!ms || !launches) && max_passes > 0) return fail(FFT_ERR_ARG, "output arrays are NULL");
+    for (int i = 0; i < max_passes; i++) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (auto &r : p->recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return fail_cuda(e, "pass timing");
+        if (r.pass < max_passes) {
+            ms[r.pass] += t;
+            launches[r.pass] += 1;
+        }
+        p->ev_free.push_back(r.a);
+        p->ev_free.push_back(r.b);
+    }
+    p->recs.clear();
+    return p->sched.npass;
 }
 
 // --------------------------------------------------------- introspection --
