@@ -124,6 +124,31 @@ int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream)
  * end-to-end path. */
 int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream);
 
+/* Transform without allocating any device memory, and without a plan.
+ * (The paper has no counterpart: this serves callers that cannot allocate.)
+ * Some callers cannot call cudaMalloc: code running inside another
+ * framework's allocator callback, where re-entering the allocator would
+ * deadlock; real-time loops that may not block on the device synchronisation
+ * cudaMalloc/cudaFree imply, nor fail on memory mid-run; processes whose
+ * device memory belongs to a pool they do not own.  This call takes device
+ * buffers `in` and `out` (same layout, alignment, aliasing and direction
+ * rules as fft_exec on a plan of (n, batch, dt, dir)) and keeps everything
+ * else -- the weight tables and the buffer that carries the data between
+ * HBM passes -- in one fixed 32 MiB __device__ array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limit: complex128 n <= 2^20, complex64 n <= 2^21 (any batch; larger n is
+ * rejected with FFT_ERR_UNSUPPORTED and a message, before any GPU work).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind; nothing in it needs to start at zero, because each call
+ * writes every table entry and workspace element before reading it.  Calls
+ * whose GPU work overlaps (for instance on two streams) race on the array
+ * and give wrong results: serialise them.  Asynchronous like fft_exec. */
+int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t batch, fft_dtype dt,
+                     fft_dir dir, void *cuda_stream);
+
 /* Release everything the plan owns.  NULL is a no-op.  Synchronises the
  * device before freeing. */
 int fft_destroy(fft_plan_t p);

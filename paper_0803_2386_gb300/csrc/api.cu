@@ -38,6 +38,11 @@ static int fail(int code, const char *fmt, ...)
     return code;
 }
 
+namespace moafft {
+// lets other translation units report through fft_last_error()
+void set_last_error_text(const char *msg) { g_last_error = msg; }
+}  // namespace moafft
+
 static int fail_cuda(cudaError_t e, const char *what)
 {
     return fail(FFT_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
