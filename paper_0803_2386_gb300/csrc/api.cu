@@ -149,6 +149,8 @@ static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
         if (req_width && req_width[i] > 0) {
             w = req_width[i];
             if (exact_log2(w) < 0) return fail(FFT_ERR_ARG, "tile width %lld is not a power of two", (long long)w);
+        } else if (p.log_r >= 4 && p.log_r <= 12) {
+            w = std::min(32, std::max(1, 4096 >> p.log_r));  // the tile kernel's width
         } else {
             w = std::max<int64_t>(1, tile_budget(dt) / R);
             w = std::min<int64_t>(w, last && p.A == 1 ? 1024 : 16);
@@ -163,7 +165,7 @@ static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
         p.tw_lo_bits = 0;
         if (!last) {
             int lm = exact_log2(p.tw_m);
-            int direct_max = dt == FFT_C128 ? 20 : 21;
+            int direct_max = dt == FFT_C128 ? 20 : 12;
             if (lm > direct_max) p.tw_lo_bits = (lm + 1) / 2;
         }
     }
@@ -411,7 +413,10 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     }
     size_t eb = elem_bytes(dt);
     if (p->sched.npass > 1) {
-        const int64_t target = (int64_t)32 << 20;  // bytes per workspace round (L2-resident)
+        // bytes per workspace round: complex64 passes are HBM-bound, so a round
+        // stays L2-resident (32 MiB); complex128 passes are FP64-bound, so
+        // larger rounds (256 MiB) cut the launch count and the wave tails
+        const int64_t target = dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)32 << 20);
         p->chunk = std::max<int64_t>(1, std::min<int64_t>(batch, target / (n * (int64_t)eb)));
         if (req_chunk > 0) p->chunk = std::min<int64_t>(batch, req_chunk);
         p->ws_bytes = p->chunk * n * (int64_t)eb;

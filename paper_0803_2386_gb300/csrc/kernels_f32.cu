@@ -1,6 +1,7 @@
 // kernels_f32.cu -- instantiations and launcher of the pass kernel for
 // float arithmetic (element type float2).
 #include "pass_kernel.cuh"
+#include "tile_kernel.cuh"
 
 namespace moafft {
 
@@ -33,8 +34,12 @@ static cudaError_t launch_dir_f32(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_f32(const PassArgs &a, int dir, cudaStream_t s);
+
+// The compile-time tile kernel where it applies, else the generic one.
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s)
 {
+    if (tile_covers(a)) return launch_tile_f32(a, dir, s);
     return dir < 0 ? launch_dir_f32<-1>(a, s) : launch_dir_f32<1>(a, s);
 }
 

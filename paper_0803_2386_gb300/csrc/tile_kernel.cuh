@@ -1,0 +1,248 @@
+// tile_kernel.cuh -- compile-time-radix HBM pass of the dimension-lifted
+// radix-2 FFT (the specialised form of pass_kernel.cuh for tiles of 2^4 to
+// 2^12 points).
+//
+// Same lifting as pass_kernel: the transform is an A x R x B array, one pass
+// runs the log2 R radix-2 stages of its group on W columns (rows in the last
+// pass) at a time.  The group is split top digit first into register
+// codelets, R = E0 * 16 * ... * 16 (sub-passes), and the memory hierarchy is
+// used level by level, as the paper lifts its loops over cache levels
+// (Ch.3): a thread's 16 registers hold one codelet's points, shared memory
+// carries the reshape-transpose between codelet digits, HBM carries it
+// between passes.
+//
+//   1. HBM -> registers: each thread loads the points of its first-digit
+//      codelets directly (element m = e*(R/E0) + mq); lanes run over the W
+//      columns first, so every load instruction reads runs of W consecutive
+//      elements.
+//   2. Codelet of radix E0, weights w_R^(mq*k), write to shared memory at
+//      the reshape-transposed position k*(R/E0) + mq.
+//   3. For each further radix-16 digit: read 16 points, codelet, weights
+//      w_S^(mq*k) (S the current sub-problem size), write back -- except
+//      after the last digit, whose results stay in registers.
+//   4. Registers -> HBM: the point with tile index k (natural order) is
+//      multiplied by the weight w_{R*B}^(b*k) the next passes need and
+//      stored in place (non-last pass), or scaled and stored through the
+//      final transpose out[rev(a) + (n/R)*k] (last pass, Eq. xihyper).
+//
+// Shared-memory positions are padded by one point per 16 (pos + pos/16),
+// which makes every exchange pattern of every tile size conflict-free.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "codelets.cuh"
+#include "internal.h"
+
+namespace moafft {
+
+__host__ __device__ constexpr int tile_width(int logr)
+{
+    return (4096 >> logr) < 1 ? 1 : ((4096 >> logr) > 32 ? 32 : (4096 >> logr));
+}
+__host__ __device__ constexpr int tile_threads(int logr) { return ((1 << logr) / 16) * tile_width(logr); }
+template <typename T>
+__host__ __device__ constexpr int tile_min_blocks(int logr)
+{
+    // c128: two 256-thread CTAs per SM (<= 128 registers); c64: three
+    return (sizeof(T) == 8 ? 512 : 768) / tile_threads(logr) > 32
+               ? 32
+               : (sizeof(T) == 8 ? 512 : 768) / tile_threads(logr);
+}
+__device__ __forceinline__ int tpad(int pos) { return pos + (pos >> 4); }
+
+// true when the compile-time tile kernel covers this pass
+inline bool tile_covers(const PassArgs &a)
+{
+    if (a.log_r < 4 || a.log_r > 12) return false;
+    const int W = tile_width(a.log_r);
+    if (a.width != W) return false;
+    if (!a.is_last) return a.B >= W && a.B % W == 0;
+    return a.A == 1 || (a.A >= W && a.A % W == 0);
+}
+
+template <typename T, int DIR, int LOGR, bool LAST>
+__global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
+    tile_kernel(PassArgs p)
+{
+    using V = typename cvec<T>::type;
+    constexpr int R = 1 << LOGR;
+    constexpr int NS = (LOGR + 3) / 4;       // sub-passes
+    constexpr int L0 = LOGR - 4 * (NS - 1);  // log2 radix of the first one
+    constexpr int E0 = 1 << L0;
+    constexpr int U = R / 16;  // threads per column
+    constexpr int W = tile_width(LOGR);
+    constexpr int G0 = 16 / E0;  // first-digit codelets per thread
+    constexpr int Q0 = R / E0;
+    static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    const V *twt = reinterpret_cast<const V *>(p.tw_tile);
+    const V *in = reinterpret_cast<const V *>(p.in);
+    V *out = reinterpret_cast<V *>(p.out);
+
+    const int tid = threadIdx.x;
+    const int w = tid % W;
+    const int u = tid / W;
+    const int64_t n = p.n;
+    const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+
+    // ---- tile origin
+    int64_t base = 0, b0 = 0, tr = 0, vrow = 0;
+    bool valid = true;
+    if constexpr (!LAST) {
+        const int64_t colgroups = p.B / W;
+        const int64_t tiles_per_tr = p.A * colgroups;
+        tr = cta / tiles_per_tr;
+        if (tr >= p.count) return;
+        const int64_t rem = cta - tr * tiles_per_tr;
+        const int64_t a = rem / colgroups;
+        b0 = (rem - a * colgroups) * W;
+        base = tr * n + a * (int64_t)R * p.B + b0 + w;  // element (m, this column) at base + m*B
+    } else {
+        int64_t a;
+        if (p.A > 1) {
+            const int64_t rowgroups = p.A / W;
+            tr = cta / rowgroups;
+            if (tr >= p.count) return;
+            const int64_t q = cta - tr * rowgroups;
+            vrow = q * W + w;
+            // a = unrev(vrow): k^(0) is the least significant digit of vrow
+            a = 0;
+            int pos = 0;
+            for (int i = 0; i <= p.npass - 2; i++) {
+                const int lb = p.pass_log[i];
+                const int64_t d = (vrow >> pos) & ((((int64_t)1) << lb) - 1);
+                pos += lb;
+                int apos = 0;
+                for (int j = i + 1; j <= p.npass - 2; j++) apos += p.pass_log[j];
+                a |= d << apos;
+            }
+        } else {
+            const int64_t tr0 = cta * W;
+            if (tr0 >= p.count) return;
+            tr = tr0 + w;
+            valid = tr < p.count;
+            a = 0;
+            vrow = 0;
+        }
+        base = tr * n + a * (int64_t)R;  // element m of this row at base + m
+    }
+    const int64_t mstride = LAST ? 1 : p.B;
+
+    V v[16];
+    // ---- 1. HBM -> registers, first digit (radix E0)
+#pragma unroll
+    for (int g = 0; g < G0; g++)
+#pragma unroll
+        for (int e = 0; e < E0; e++) {
+            const int m = e * Q0 + g * U + u;
+            if (valid) v[g * E0 + e] = in[base + (int64_t)m * mstride];
+            else { v[g * E0 + e].x = 0; v[g * E0 + e].y = 0; }
+        }
+
+    // ---- 2. first-digit codelets
+#pragma unroll
+    for (int g = 0; g < G0; g++) {
+        dft_codelet<DIR, L0>(&v[g * E0]);
+        if constexpr (NS > 1) {
+            const int mq = g * U + u;
+#pragma unroll
+            for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], __ldg(twt + mq * k));
+        }
+    }
+
+    // ---- 3. radix-16 digits through shared memory
+    if constexpr (NS > 1) {
+#pragma unroll
+        for (int g = 0; g < G0; g++)
+#pragma unroll
+            for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + g * U + u) * W + w] = v[g * E0 + k];
+        __syncthreads();
+        int S = Q0;
+#pragma unroll
+        for (int j = 1; j < NS; j++) {
+            const int Q = S / 16;
+            const int pre = u / Q, mq = u % Q;
+            const int pos0 = pre * S + mq;
+#pragma unroll
+            for (int e = 0; e < 16; e++) v[e] = tile[tpad(pos0 + e * Q) * W + w];
+            dft_codelet<DIR, 4>(v);
+            if (j < NS - 1) {
+                if (mq != 0) {
+                    const int step = R / S;
+#pragma unroll
+                    for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], __ldg(twt + mq * k * step));
+                }
+                // each thread rewrites exactly the positions it read
+#pragma unroll
+                for (int k = 0; k < 16; k++) tile[tpad(pos0 + k * Q) * W + w] = v[k];
+                __syncthreads();
+            }
+            S = Q;
+        }
+    }
+
+    // ---- 4. registers -> HBM
+    // this thread's points have natural tile index k = rev(u) + U*j (j < 16):
+    // u holds the earlier digits with the first one most significant
+    int revu = 0;
+    if constexpr (NS > 1) {
+        // u = k_0 * 16^(NS-2) + k_1 * 16^(NS-3) + ... + k_(NS-2)  (k_0 < E0)
+        // rev(u) = k_0 + E0*(k_1 + 16*(k_2 + ...))
+        int rem = u;
+        int digits[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = NS - 2; j >= 1; j--) {
+            digits[j] = rem & 15;
+            rem >>= 4;
+        }
+        digits[0] = rem;
+        revu = digits[0];
+        int shift = L0;
+#pragma unroll
+        for (int j = 1; j <= NS - 2; j++) {
+            revu |= digits[j] << shift;
+            shift += 4;
+        }
+    }
+    if (!valid) return;
+    if constexpr (!LAST) {
+        const int64_t b = b0 + w;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int kk = revu + U * j;  // NS == 1: R = 16, U = 1, revu = 0
+            V x = v[j];
+            const int64_t ex = b * (int64_t)kk;
+            if (ex != 0) {
+                V wv;
+                if (p.tw_lo_bits == 0) {
+                    wv = __ldg(reinterpret_cast<const V *>(p.tw_pass) + ex);
+                } else {
+                    const V wa = __ldg(reinterpret_cast<const V *>(p.tw_pass) +
+                                       (ex & ((((int64_t)1) << p.tw_lo_bits) - 1)));
+                    const V wb = __ldg(reinterpret_cast<const V *>(p.tw_hi) + (ex >> p.tw_lo_bits));
+                    wv = c_mul(wa, wb);
+                }
+                x = c_tw<DIR>(x, wv);
+            }
+            out[base + (int64_t)kk * p.B] = x;
+        }
+    } else {
+        const int64_t obase = tr * n + vrow;
+        const int64_t kstride = n / R;
+        const T sc = (T)p.scale;
+        const bool scale = p.scale != 1.0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int kk = revu + U * j;
+            V x = v[j];
+            if (scale) { x.x *= sc; x.y *= sc; }
+            out[obase + (int64_t)kk * kstride] = x;
+        }
+    }
+}
+
+}  // namespace moafft
