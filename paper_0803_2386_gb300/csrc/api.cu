@@ -260,15 +260,27 @@ static std::string schedule_json(const Schedule &s)
 
 // ---------------------------------------------------------------- plans ---
 
+// One length of the batch: a plain plan has one class (dense layout); an
+// uneven plan (fft_plan_many) has one class per distinct length, whose
+// transforms are located through a device table of element offsets.
+struct SizeClass {
+    int64_t n = 1;
+    int64_t count = 0;
+    Schedule sched;
+    int64_t chunk = 1;           // transforms per workspace round
+    std::vector<int64_t> offs;   // element offsets (uneven plans)
+    DevBuf d_off;                // the same on the device
+};
+
 struct fft_plan_s {
-    int64_t n = 0, batch = 0;
+    int64_t n = 0, batch = 0;  // n = 0 for an uneven plan
+    int64_t total = 0;         // elements in one buffer
     fft_dtype dt = FFT_C64;
     fft_dir dir = FFT_FORWARD;
     fft_form form = FFT_FORM_PLAIN;
-    Schedule sched;
-    int64_t chunk = 1;  // transforms per workspace round
-    DevBuf tw;          // twiddle arena
-    DevBuf ws;          // inter-pass workspace
+    std::vector<SizeClass> classes;
+    DevBuf tw;  // twiddle arena
+    DevBuf ws;  // inter-pass workspace
     int64_t ws_bytes = 0;
     int device = 0;
     // kernel timing (fft_plan_profile)
@@ -285,6 +297,13 @@ struct fft_plan_s {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
                 ev_d2h[2] = {nullptr, nullptr};
+    // uneven plans replay one captured graph per (in, out, adjoint)
+    bool use_graph = false;
+    cudaStream_t s_capture = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void *g_in = nullptr;
+    void *g_out = nullptr;
+    int g_adj = -1;
 };
 
 static cudaEvent_t take_event(fft_plan_s *p)
@@ -318,52 +337,63 @@ size_t pass_smem_bytes(const PassArgs &a, size_t eb)
 }
 }  // namespace moafft
 
+static int64_t class_launches(const SizeClass &c)
+{
+    if (c.sched.npass == 1) return 1;
+    return (c.count + c.chunk - 1) / c.chunk * c.sched.npass;
+}
+
 static int64_t launches_per_exec(const fft_plan_s *p)
 {
-    if (p->sched.npass == 1) return 1;
-    int64_t chunks = (p->batch + p->chunk - 1) / p->chunk;
-    return chunks * p->sched.npass;
+    int64_t k = 0;
+    for (const auto &c : p->classes) k += class_launches(c);
+    return k;
 }
 
 static int make_tables(fft_plan_s *p)
 {
-    // arena layout: for each pass, tile table (R entries), then pass table(s)
+    // arena layout: per class, per pass, the tile table (R entries) and the
+    // pass table(s)
     size_t eb = elem_bytes(p->dt);
     size_t off = 0;
-    for (int i = 0; i < p->sched.npass; i++) {
-        PassDesc &d = p->sched.pass[i];
-        d.tw_tile_off = off;
-        off += (size_t)1 << d.log_r;
-        if (i < p->sched.npass - 1) {
-            d.tw_pass_off = off;
-            if (d.tw_lo_bits == 0) off += (size_t)d.tw_m;
-            else {
-                off += (size_t)1 << d.tw_lo_bits;
-                d.tw_hi_off = off;
-                off += (size_t)(d.tw_m >> d.tw_lo_bits);
+    for (auto &c : p->classes) {
+        for (int i = 0; i < c.sched.npass; i++) {
+            PassDesc &d = c.sched.pass[i];
+            d.tw_tile_off = off;
+            off += (size_t)1 << d.log_r;
+            if (i < c.sched.npass - 1) {
+                d.tw_pass_off = off;
+                if (d.tw_lo_bits == 0) off += (size_t)d.tw_m;
+                else {
+                    off += (size_t)1 << d.tw_lo_bits;
+                    d.tw_hi_off = off;
+                    off += (size_t)(d.tw_m >> d.tw_lo_bits);
+                }
             }
         }
     }
     int st = dev_alloc(p->tw, off * eb, "twiddle tables");
     if (st != FFT_OK) return st;
-    for (int i = 0; i < p->sched.npass; i++) {
-        PassDesc &d = p->sched.pass[i];
-        int64_t R = (int64_t)1 << d.log_r;
-        auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
-            if (p->dt == FFT_C128)
-                return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
-            return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
-        };
-        cudaError_t e = gen(d.tw_tile_off, R, R, 1);
-        if (e == cudaSuccess && i < p->sched.npass - 1) {
-            if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
-            else {
-                e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
-                if (e == cudaSuccess)
-                    e = gen(d.tw_hi_off, d.tw_m >> d.tw_lo_bits, d.tw_m, (int64_t)1 << d.tw_lo_bits);
+    for (auto &c : p->classes) {
+        for (int i = 0; i < c.sched.npass; i++) {
+            PassDesc &d = c.sched.pass[i];
+            int64_t R = (int64_t)1 << d.log_r;
+            auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
+                if (p->dt == FFT_C128)
+                    return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
+                return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
+            };
+            cudaError_t e = gen(d.tw_tile_off, R, R, 1);
+            if (e == cudaSuccess && i < c.sched.npass - 1) {
+                if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
+                else {
+                    e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
+                    if (e == cudaSuccess)
+                        e = gen(d.tw_hi_off, d.tw_m >> d.tw_lo_bits, d.tw_m, (int64_t)1 << d.tw_lo_bits);
+                }
             }
+            if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
         }
-        if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail_cuda(e, "twiddle generation (sync)");
@@ -378,6 +408,67 @@ static int check_common(int64_t n, fft_dtype dt, fft_dir dir)
     if (exact_log2(n) < 0) return fail(FFT_ERR_NOT_POW2, "n = %lld is not a power of two", (long long)n);
     if (exact_log2(n) > 30) return fail(FFT_ERR_UNSUPPORTED, "n = 2^%d exceeds 2^30", exact_log2(n));
     return FFT_OK;
+}
+
+static void destroy_plan(fft_plan_s *p)
+{
+    dev_free(p->ws);
+    dev_free(p->tw);
+    for (auto &c : p->classes) dev_free(c.d_off);
+    for (int k = 0; k < 2; k++) {
+        dev_free(p->stage_in[k]);
+        dev_free(p->stage_out[k]);
+        if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
+        if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+        if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
+    }
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->s_capture) cudaStreamDestroy(p->s_capture);
+    for (auto &r : p->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto ev : p->ev_free) cudaEventDestroy(ev);
+    delete p;
+}
+
+// shared tail of plan creation: device, workspace, offsets, tables
+static int finish_plan(fft_plan_s *p, int64_t req_chunk)
+{
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail_cuda(e, "cudaGetDevice");
+    }
+    size_t eb = elem_bytes(p->dt);
+    // complex64 passes are HBM-bound, so a workspace round stays L2-resident
+    // (32 MiB); complex128 passes are FP64-bound, so larger rounds (256 MiB)
+    // cut the launch count and the wave tails
+    const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)32 << 20);
+    int64_t ws = 0;
+    for (auto &c : p->classes) {
+        if (c.sched.npass > 1) {
+            c.chunk = std::max<int64_t>(1, std::min<int64_t>(c.count, target / (c.n * (int64_t)eb)));
+            if (req_chunk > 0) c.chunk = std::min<int64_t>(c.count, req_chunk);
+            ws = std::max<int64_t>(ws, c.chunk * c.n * (int64_t)eb);
+        } else {
+            c.chunk = c.count;
+        }
+        if (!c.offs.empty()) {
+            int st = dev_alloc(c.d_off, c.offs.size() * sizeof(int64_t), "offset table");
+            if (st != FFT_OK) return st;
+            e = cudaMemcpy(c.d_off.ptr, c.offs.data(), c.offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail_cuda(e, "offset table upload");
+        }
+    }
+    if (ws > 0) {
+        p->ws_bytes = ws;
+        int st = dev_alloc(p->ws, (size_t)ws, "workspace");
+        if (st != FFT_OK) return st;
+    }
+    return make_tables(p);
 }
 
 extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,
@@ -396,43 +487,19 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     if (!p) return fail(FFT_ERR_ALLOC, "host allocation of the plan failed");
     p->n = n;
     p->batch = batch;
+    p->total = n * batch;
     p->dt = dt;
     p->dir = dir;
     p->form = form;
+    p->classes.resize(1);
+    SizeClass &c = p->classes[0];
+    c.n = n;
+    c.count = batch;
     int64_t req_chunk = 0;
-    st = build_schedule(p->sched, n, dt, schedule, &req_chunk);
+    st = build_schedule(c.sched, n, dt, schedule, &req_chunk);
+    if (st == FFT_OK) st = finish_plan(p, req_chunk);
     if (st != FFT_OK) {
-        delete p;
-        return st;
-    }
-    cudaError_t e = cudaGetDevice(&p->device);
-    if (e != cudaSuccess) {
-        delete p;
-        cudaGetLastError();
-        return fail_cuda(e, "cudaGetDevice");
-    }
-    size_t eb = elem_bytes(dt);
-    if (p->sched.npass > 1) {
-        // bytes per workspace round: complex64 passes are HBM-bound, so a round
-        // stays L2-resident (32 MiB); complex128 passes are FP64-bound, so
-        // larger rounds (256 MiB) cut the launch count and the wave tails
-        const int64_t target = dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)32 << 20);
-        p->chunk = std::max<int64_t>(1, std::min<int64_t>(batch, target / (n * (int64_t)eb)));
-        if (req_chunk > 0) p->chunk = std::min<int64_t>(batch, req_chunk);
-        p->ws_bytes = p->chunk * n * (int64_t)eb;
-        st = dev_alloc(p->ws, (size_t)p->ws_bytes, "workspace");
-        if (st != FFT_OK) {
-            delete p;
-            return st;
-        }
-    } else {
-        p->chunk = batch;
-    }
-    st = make_tables(p);
-    if (st != FFT_OK) {
-        dev_free(p->ws);
-        dev_free(p->tw);
-        delete p;
+        destroy_plan(p);
         return st;
     }
     *out = p;
@@ -454,30 +521,50 @@ extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t coun
         int st = check_common(sizes[i], dt, dir);
         if (st != FFT_OK) return st;
     }
-    return fail(FFT_ERR_UNSUPPORTED, "fft_plan_many not available in this build");
+    fft_plan_s *p = new (std::nothrow) fft_plan_s();
+    if (!p) return fail(FFT_ERR_ALLOC, "host allocation of the plan failed");
+    p->n = 0;
+    p->batch = count;
+    p->dt = dt;
+    p->dir = dir;
+    p->use_graph = true;
+    // group by length (ascending); each class keeps its transforms' offsets
+    int64_t off = 0;
+    std::vector<int> cls_of(31, -1);
+    for (int64_t i = 0; i < count; i++) {
+        int t = exact_log2(sizes[i]);
+        if (cls_of[t] < 0) {
+            cls_of[t] = (int)p->classes.size();
+            p->classes.emplace_back();
+            p->classes.back().n = sizes[i];
+        }
+        SizeClass &c = p->classes[cls_of[t]];
+        c.offs.push_back(off);
+        c.count++;
+        off += sizes[i];
+    }
+    p->total = off;
+    std::sort(p->classes.begin(), p->classes.end(),
+              [](const SizeClass &a, const SizeClass &b) { return a.n < b.n; });
+    int st = FFT_OK;
+    for (auto &c : p->classes) {
+        st = build_schedule(c.sched, c.n, dt, nullptr, nullptr);
+        if (st != FFT_OK) break;
+    }
+    if (st == FFT_OK) st = finish_plan(p, 0);
+    if (st != FFT_OK) {
+        destroy_plan(p);
+        return st;
+    }
+    *out = p;
+    return FFT_OK;
 }
 
 extern "C" int fft_destroy(fft_plan_t p)
 {
     if (!p) return FFT_OK;
     cudaError_t e = cudaDeviceSynchronize();
-    dev_free(p->ws);
-    dev_free(p->tw);
-    for (int k = 0; k < 2; k++) {
-        dev_free(p->stage_in[k]);
-        dev_free(p->stage_out[k]);
-        if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
-        if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
-        if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
-    }
-    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
-    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
-    for (auto &r : p->recs) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
-    for (auto ev : p->ev_free) cudaEventDestroy(ev);
-    delete p;
+    destroy_plan(p);
     if (e != cudaSuccess) return fail_cuda(e, "fft_destroy (sync)");
     return FFT_OK;
 }
@@ -499,27 +586,34 @@ static int check_device_ptr(const void *ptr, size_t align, const char *what)
     return FFT_OK;
 }
 
-// Transforms [b0, b0 + cnt) of the batch, device buffers already checked.
-// in/out point at transform b0.
-static int exec_range(fft_plan_t p, const void *in, void *out, int64_t cnt, int sign, double scale,
-                      cudaStream_t s)
+// Transforms [t0, t0 + cnt) of one class, device buffers already checked.
+// Dense classes: in/out point at the class's transform t0.  Uneven classes:
+// in/out are the whole packed buffers and the offset table locates each
+// transform.
+static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *out, int64_t t0,
+                      int64_t cnt, int sign, cudaStream_t s)
 {
     size_t eb = elem_bytes(p->dt);
-    const Schedule &S = p->sched;
+    const Schedule &S = C.sched;
+    const double scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)C.n : 1.0;
+    const bool ragged = C.d_off.ptr != nullptr;
     PassArgs a;
     memset(&a, 0, sizeof a);
-    a.n = p->n;
+    a.n = C.n;
     a.npass = S.npass;
     for (int i = 0; i < S.npass; i++) a.pass_log[i] = S.pass[i].log_r;
-    const int64_t chunk = S.npass > 1 ? p->chunk : cnt;
+    const int64_t chunk = S.npass > 1 ? C.chunk : cnt;
     for (int64_t c0 = 0; c0 < cnt; c0 += chunk) {
         int64_t c = std::min(chunk, cnt - c0);
-        const char *src = (const char *)in + (size_t)c0 * p->n * eb;
-        char *dst = (char *)out + (size_t)c0 * p->n * eb;
+        const char *src = ragged ? (const char *)in : (const char *)in + (size_t)(t0 + c0) * C.n * eb;
+        char *dst = ragged ? (char *)out : (char *)out + (size_t)(t0 + c0) * C.n * eb;
+        const int64_t *off = ragged ? (const int64_t *)C.d_off.ptr + t0 + c0 : nullptr;
         for (int i = 0; i < S.npass; i++) {
             const PassDesc &d = S.pass[i];
             a.in = (i == 0) ? (const void *)src : p->ws.ptr;
             a.out = (i == S.npass - 1) ? (void *)dst : p->ws.ptr;
+            a.in_off = (i == 0) ? off : nullptr;
+            a.out_off = (i == S.npass - 1) ? off : nullptr;
             a.count = c;
             a.log_r = d.log_r;
             a.width = d.width;
@@ -550,13 +644,70 @@ static int exec_range(fft_plan_t p, const void *in, void *out, int64_t cnt, int 
     return FFT_OK;
 }
 
-static void direction_of(fft_plan_t p, bool adjoint, int *sign, double *scale)
+static int exec_all(fft_plan_t p, const void *in, void *out, int sign, cudaStream_t s)
+{
+    for (const auto &c : p->classes) {
+        int st = exec_class(p, c, in, out, 0, c.count, sign, s);
+        if (st != FFT_OK) return st;
+    }
+    return FFT_OK;
+}
+
+// Uneven plans: capture the whole launch sequence once per (in, out, sign)
+// and replay it as one graph launch.
+static int exec_graph(fft_plan_t p, const void *in, void *out, int sign, cudaStream_t s)
+{
+    if (!(p->gexec && p->g_in == in && p->g_out == out && p->g_adj == sign)) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        cudaError_t e = cudaSuccess;
+        if (!p->s_capture) e = cudaStreamCreateWithFlags(&p->s_capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail_cuda(e, "capture stream");
+        e = cudaStreamBeginCapture(p->s_capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
+        const bool prof = p->profile;
+        p->profile = false;
+        int st = exec_all(p, in, out, sign, p->s_capture);
+        p->profile = prof;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->s_capture, &g);
+        if (st != FFT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return fail_cuda(e, "cudaGraphInstantiate");
+        }
+        p->g_in = in;
+        p->g_out = out;
+        p->g_adj = sign;
+    }
+    fft_plan_s::Rec rec{0, nullptr, nullptr};
+    if (p->profile) {
+        rec.a = take_event(p);
+        rec.b = take_event(p);
+        if (rec.a) cudaEventRecord(rec.a, s);
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGraphLaunch");
+    if (p->profile && rec.a && rec.b) {
+        cudaEventRecord(rec.b, s);
+        p->recs.push_back(rec);
+    }
+    return FFT_OK;
+}
+
+static int direction_sign(fft_plan_t p, bool adjoint)
 {
     // forward s=-1 unscaled, inverse s=+1 x 1/n; the adjoint swaps the sign
     // and keeps the scaling.
-    *sign = (int)p->dir;
-    if (adjoint) *sign = -*sign;
-    *scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)p->n : 1.0;
+    return adjoint ? -(int)p->dir : (int)p->dir;
 }
 
 static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoint)
@@ -567,14 +718,13 @@ static int run(fft_plan_t p, const void *in, void *out, void *stream, bool adjoi
     if (st != FFT_OK) return st;
     st = check_device_ptr(out, eb, "out");
     if (st != FFT_OK) return st;
-    const size_t bytes = (size_t)p->n * (size_t)p->batch * eb;
+    const size_t bytes = (size_t)p->total * eb;
     uintptr_t a0 = (uintptr_t)in, a1 = a0 + bytes, b0 = (uintptr_t)out, b1 = b0 + bytes;
     if (in != out && a0 < b1 && b0 < a1)
         return fail(FFT_ERR_ALIAS, "in and out overlap without being identical");
-    int sign;
-    double scale;
-    direction_of(p, adjoint, &sign, &scale);
-    return exec_range(p, in, out, p->batch, sign, scale, (cudaStream_t)stream);
+    const int sign = direction_sign(p, adjoint);
+    if (p->use_graph) return exec_graph(p, in, out, sign, (cudaStream_t)stream);
+    return exec_all(p, in, out, sign, (cudaStream_t)stream);
 }
 
 static int check_host_ptr(const void *ptr, const char *what)
@@ -621,16 +771,17 @@ static int setup_staging(fft_plan_t p)
 static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
 {
     if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    if (p->classes.size() != 1 || p->n == 0)
+        return fail(FFT_ERR_UNSUPPORTED, "fft_exec_host takes plans of one length (fft_plan / fft_plan_ex)");
     int st = check_host_ptr(in, "in");
     if (st == FFT_OK) st = check_host_ptr(out, "out");
     if (st == FFT_OK) st = setup_staging(p);
     if (st != FFT_OK) return st;
-    int sign;
-    double scale;
-    direction_of(p, false, &sign, &scale);
+    const int sign = direction_sign(p, false);
     size_t eb = elem_bytes(p->dt);
     cudaStream_t cs = (cudaStream_t)stream;
     bool used[2] = {false, false};
+    const SizeClass &C = p->classes[0];
     for (int64_t b0 = 0, i = 0; b0 < p->batch; b0 += p->stage_tr, i++) {
         int k = (int)(i & 1);
         int64_t cnt = std::min(p->stage_tr, p->batch - b0);
@@ -644,7 +795,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->ev_h2d[k], 0);
         if (e == cudaSuccess && used[k]) e = cudaStreamWaitEvent(cs, p->ev_d2h[k], 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (copy in)");
-        st = exec_range(p, p->stage_in[k].ptr, p->stage_out[k].ptr, cnt, sign, scale, cs);
+        st = exec_class(p, C, p->stage_in[k].ptr, p->stage_out[k].ptr, 0, cnt, sign, cs);
         if (st != FFT_OK) return st;
         e = cudaEventRecord(p->ev_comp[k], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0);
@@ -706,7 +857,9 @@ extern "C" int fft_plan_pass_times(fft_plan_t p, double *ms, int64_t *launches, 
         p->ev_free.push_back(r.b);
     }
     p->recs.clear();
-    return p->sched.npass;
+    int np = 0;
+    for (const auto &c : p->classes) np = std::max(np, c.sched.npass);
+    return p->use_graph ? 1 : np;
 }
 
 // --------------------------------------------------------- introspection --
@@ -738,10 +891,21 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
 {
     if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
     std::string j = "{\"n\": " + std::to_string(p->n) + ", \"batch\": " + std::to_string(p->batch) +
-                    ", \"dtype\": \"" + (p->dt == FFT_C128 ? "c128" : "c64") + "\", \"chunk\": " +
-                    std::to_string(p->chunk) + ", \"workspace_bytes\": " + std::to_string(p->ws_bytes) +
-                    ", \"launches\": " + std::to_string(launches_per_exec(p)) +
-                    ", \"schedule\": " + schedule_json(p->sched) + "}";
+                    ", \"dtype\": \"" + (p->dt == FFT_C128 ? "c128" : "c64") + "\", \"workspace_bytes\": " +
+                    std::to_string(p->ws_bytes) + ", \"launches\": " + std::to_string(launches_per_exec(p)) +
+                    ", \"graph\": " + (p->use_graph ? "true" : "false");
+    if (p->classes.size() == 1) {
+        j += ", \"chunk\": " + std::to_string(p->classes[0].chunk) + ", \"schedule\": " +
+             schedule_json(p->classes[0].sched);
+    }
+    j += ", \"classes\": [";
+    for (size_t i = 0; i < p->classes.size(); i++) {
+        const SizeClass &c = p->classes[i];
+        j += (i ? ", " : "") + std::string("{\"n\": ") + std::to_string(c.n) + ", \"count\": " +
+             std::to_string(c.count) + ", \"chunk\": " + std::to_string(c.chunk) + ", \"passes\": " +
+             std::to_string(c.sched.npass) + "}";
+    }
+    j += "]}";
     return put(buf, len, j);
 }
 

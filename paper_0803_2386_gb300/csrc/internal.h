@@ -60,6 +60,10 @@ struct PassArgs {
     const void *tw_hi;          // w_M^(e << lo_bits) (two-level)
     int tw_lo_bits;
     double scale;               // applied in the last pass (1 or 1/n)
+    // ragged batches: element offset of transform tr in `in` (loads) and in
+    // `out` (stores); NULL means the dense layout tr * n
+    const int64_t *in_off;
+    const int64_t *out_off;
 };
 
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)

@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
         const int64_t rem = cta - tr * tiles_per_tr;
         const int64_t a = rem / colgroups;
         const int64_t b0 = (rem - a * colgroups) * W;
-        const int64_t base = tr * n + a * (int64_t)R * p.B + b0;
+        const int64_t inner = a * (int64_t)R * p.B + b0;
+        const int64_t base = (p.in_off ? p.in_off[tr] : tr * n) + inner;
+        const int64_t sbase = (p.out_off ? p.out_off[tr] : tr * n) + inner;
         for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
             int w = idx % W, m = idx / W;
             tile[spad(m * W + w)] = in[base + (int64_t)m * p.B + w];
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
             V v = tile[spad(tile_pos(k, p) * W + w)];
             int64_t e = (b0 + w) * (int64_t)k;  // w_{R*B}^(b*k)
             if (e != 0) v = c_tw<DIR>(v, pass_weight<T, DIR>(p, e));
-            out[base + (int64_t)k * p.B + w] = v;
+            out[sbase + (int64_t)k * p.B + w] = v;
         }
     } else {
         // ---- row tile: W rows with consecutive rev(a) (or W transforms when A = 1)
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
             if (p.A > 1) { tr = tr0; a = unrev_rows(q * W + w, p); }
             else { tr = tr0 + w; a = 0; }
             V v;
-            if (tr < p.count) v = in[tr * n + a * R + m];
+            if (tr < p.count) v = in[(p.in_off ? p.in_off[tr] : tr * n) + a * R + m];
             else { v.x = 0; v.y = 0; }
             tile[spad(m * W + w)] = v;
         }
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
             if (tr >= p.count) continue;
             V v = tile[spad(tile_pos(k, p) * W + w)];
             if (p.scale != 1.0) { v.x *= sc; v.y *= sc; }
-            out[tr * n + v_row + stride_k * k] = v;
+            out[(p.out_off ? p.out_off[tr] : tr * n) + v_row + stride_k * k] = v;
         }
     }
 }

@@ -89,8 +89,9 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     const int64_t n = p.n;
     const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
 
-    // ---- tile origin
-    int64_t base = 0, b0 = 0, tr = 0, vrow = 0;
+    // ---- tile origin (load base; the store base differs only for ragged
+    // batches, whose transforms sit at in_off[tr] / out_off[tr])
+    int64_t base = 0, sbase = 0, b0 = 0, tr = 0, vrow = 0;
     bool valid = true;
     if constexpr (!LAST) {
         const int64_t colgroups = p.B / W;
@@ -100,7 +101,9 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
         const int64_t rem = cta - tr * tiles_per_tr;
         const int64_t a = rem / colgroups;
         b0 = (rem - a * colgroups) * W;
-        base = tr * n + a * (int64_t)R * p.B + b0 + w;  // element (m, this column) at base + m*B
+        const int64_t inner = a * (int64_t)R * p.B + b0 + w;  // element (m, this column) at base + m*B
+        base = (p.in_off ? __ldg(p.in_off + tr) : tr * n) + inner;
+        sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n) + inner;
     } else {
         int64_t a;
         if (p.A > 1) {
@@ -128,7 +131,10 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
             a = 0;
             vrow = 0;
         }
-        base = tr * n + a * (int64_t)R;  // element m of this row at base + m
+        if (valid) {
+            base = (p.in_off ? __ldg(p.in_off + tr) : tr * n) + a * (int64_t)R;  // element m at base + m
+            sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n);
+        }
     }
     const int64_t mstride = LAST ? 1 : p.B;
 
@@ -228,10 +234,10 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
                 }
                 x = c_tw<DIR>(x, wv);
             }
-            out[base + (int64_t)kk * p.B] = x;
+            out[sbase + (int64_t)kk * p.B] = x;
         }
     } else {
-        const int64_t obase = tr * n + vrow;
+        const int64_t obase = sbase + vrow;
         const int64_t kstride = n / R;
         const T sc = (T)p.scale;
         const bool scale = p.scale != 1.0;
