@@ -149,6 +149,12 @@ int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream);
 int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t batch, fft_dtype dt,
                      fft_dir dir, void *cuda_stream);
 
+/* Synchronise the device and report what the plan's kernels recorded:
+ * FFT_ERR_TIMEOUT if a bounded device-side wait (the tensor-core form's
+ * mbarrier waits) gave up since the last check (the flag is then cleared),
+ * FFT_ERR_CUDA if the device reports an error, else FFT_OK. */
+int fft_plan_check(fft_plan_t p);
+
 /* Release everything the plan owns.  NULL is a no-op.  Synchronises the
  * device before freeing. */
 int fft_destroy(fft_plan_t p);

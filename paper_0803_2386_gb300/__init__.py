@@ -40,7 +40,7 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
 
 # every symbol include/moafft.h declares
 EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_exec", "fft_exec_adjoint",
-           "fft_exec_host", "fft_exec_noalloc", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
+           "fft_exec_host", "fft_exec_noalloc", "fft_plan_check", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
            "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_version"]
 
 _LIB = None
@@ -79,6 +79,7 @@ def lib():
             "fft_exec_adjoint": (i32, [vp, vp, vp, vp]),
             "fft_exec_host": (i32, [vp, vp, vp, vp]),
             "fft_exec_noalloc": (i32, [vp, vp, i64, i64, i32, i32, vp]),
+            "fft_plan_check": (i32, [vp]),
             "fft_plan_profile": (i32, [vp, i32]),
             "fft_plan_pass_times": (i32, [vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(i64), i32]),
@@ -183,6 +184,11 @@ def fft_exec_noalloc(inp, out, n: int, batch: int, dtype: int, direction: int = 
     scratch; see include/moafft.h for the limits)."""
     _check(lib().fft_exec_noalloc(_ptr(inp), _ptr(out), n, batch, dtype, direction,
                                   _stream(stream, inp, out)))
+
+
+def fft_plan_check(plan: int):
+    """Synchronise; raise on a recorded device-side timeout or CUDA error."""
+    _check(lib().fft_plan_check(plan))
 
 
 def fft_plan_profile(plan: int, enable: bool = True):

@@ -279,8 +279,9 @@ struct fft_plan_s {
     fft_dir dir = FFT_FORWARD;
     fft_form form = FFT_FORM_PLAIN;
     std::vector<SizeClass> classes;
-    DevBuf tw;  // twiddle arena
-    DevBuf ws;  // inter-pass workspace
+    DevBuf tw;   // twiddle arena
+    DevBuf ws;   // inter-pass workspace
+    DevBuf err;  // int set by a kernel whose bounded wait gave up
     int64_t ws_bytes = 0;
     int device = 0;
     // kernel timing (fft_plan_profile)
@@ -414,6 +415,7 @@ static void destroy_plan(fft_plan_s *p)
 {
     dev_free(p->ws);
     dev_free(p->tw);
+    dev_free(p->err);
     for (auto &c : p->classes) dev_free(c.d_off);
     for (int k = 0; k < 2; k++) {
         dev_free(p->stage_in[k]);
@@ -468,6 +470,10 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
         int st = dev_alloc(p->ws, (size_t)ws, "workspace");
         if (st != FFT_OK) return st;
     }
+    int st = dev_alloc(p->err, sizeof(int), "error word");
+    if (st != FFT_OK) return st;
+    e = cudaMemset(p->err.ptr, 0, sizeof(int));
+    if (e != cudaSuccess) return fail_cuda(e, "error word");
     return make_tables(p);
 }
 
@@ -481,8 +487,8 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     if (batch < 1) return fail(FFT_ERR_ARG, "batch = %lld < 1", (long long)batch);
     if (form != FFT_FORM_PLAIN && form != FFT_FORM_TC_FP16 && form != FFT_FORM_TC_BF16)
         return fail(FFT_ERR_ARG, "unknown form %d", (int)form);
-    if (form != FFT_FORM_PLAIN)
-        return fail(FFT_ERR_UNSUPPORTED, "tensor-core form not available in this build");
+    if (form != FFT_FORM_PLAIN && dt != FFT_C64)
+        return fail(FFT_ERR_UNSUPPORTED, "the tensor-core forms take complex64 data");
     fft_plan_s *p = new (std::nothrow) fft_plan_s();
     if (!p) return fail(FFT_ERR_ALLOC, "host allocation of the plan failed");
     p->n = n;
@@ -627,13 +633,18 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
             a.tw_lo_bits = d.tw_lo_bits;
             a.scale = a.is_last ? scale : 1.0;
+            a.err = (int *)p->err.ptr;
             fft_plan_s::Rec rec{i, nullptr, nullptr};
             if (p->profile) {
                 rec.a = take_event(p);
                 rec.b = take_event(p);
                 if (rec.a) cudaEventRecord(rec.a, s);
             }
-            cudaError_t e = p->dt == FFT_C128 ? launch_pass_f64(a, sign, s) : launch_pass_f32(a, sign, s);
+            cudaError_t e;
+            if (p->dt == FFT_C128) e = launch_pass_f64(a, sign, s);
+            else if (p->form != FFT_FORM_PLAIN && tc_covers(a))
+                e = launch_tc_f32(a, sign, p->form == FFT_FORM_TC_BF16, s);
+            else e = launch_pass_f32(a, sign, s);
             if (e != cudaSuccess) return fail_cuda(e, "pass launch");
             if (p->profile && rec.a && rec.b) {
                 cudaEventRecord(rec.b, s);
@@ -829,6 +840,21 @@ extern "C" int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda
     return run_host(p, in, out, cuda_stream);
 }
 
+extern "C" int fft_plan_check(fft_plan_t p)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail_cuda(e, "fft_plan_check");
+    int flag = 0;
+    e = cudaMemcpy(&flag, p->err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(e, "fft_plan_check (read)");
+    if (flag) {
+        cudaMemset(p->err.ptr, 0, sizeof(int));
+        return fail(FFT_ERR_TIMEOUT, "a bounded device-side wait of this plan's kernels gave up");
+    }
+    return FFT_OK;
+}
+
 extern "C" int fft_plan_profile(fft_plan_t p, int enable)
 {
     if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
@@ -893,7 +919,9 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
     std::string j = "{\"n\": " + std::to_string(p->n) + ", \"batch\": " + std::to_string(p->batch) +
                     ", \"dtype\": \"" + (p->dt == FFT_C128 ? "c128" : "c64") + "\", \"workspace_bytes\": " +
                     std::to_string(p->ws_bytes) + ", \"launches\": " + std::to_string(launches_per_exec(p)) +
-                    ", \"graph\": " + (p->use_graph ? "true" : "false");
+                    ", \"graph\": " + (p->use_graph ? "true" : "false") + ", \"form\": \"" +
+                    (p->form == FFT_FORM_TC_FP16 ? "tc_fp16" : p->form == FFT_FORM_TC_BF16 ? "tc_bf16" : "plain") +
+                    "\"";
     if (p->classes.size() == 1) {
         j += ", \"chunk\": " + std::to_string(p->classes[0].chunk) + ", \"schedule\": " +
              schedule_json(p->classes[0].sched);

@@ -64,11 +64,17 @@ struct PassArgs {
     // `out` (stores); NULL means the dense layout tr * n
     const int64_t *in_off;
     const int64_t *out_off;
+    // device word set to 1 when a bounded wait inside a kernel gave up
+    int *err;
 };
 
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);
 cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);
+// tensor-core radix-16 form (tc_f32.cu); returns cudaErrorNotSupported when
+// the pass is not a tile it covers
+bool tc_covers(const PassArgs &a);
+cudaError_t launch_tc_f32(const PassArgs &a, int dir, bool bf16, cudaStream_t s);
 
 // twiddle generation (twiddle.cu): dst[j] = exp(-2*pi*i * j*stride / m),
 // j < count, computed in FP64 with sincospi; f32 variant rounds once.

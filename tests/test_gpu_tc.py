@@ -1,0 +1,82 @@
+"""Precision form: radix-16 DFT digits as tensor-core (tcgen05) products with
+split FP16 / BF16 operands and FP32 accumulation, complex64 data.
+Tolerance (relative L2 per transform against the FP64 oracle): 1e-5 * log2 n."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_0803_2386_gb300 as M
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FORMS = [M.FFT_FORM_TC_FP16, M.FFT_FORM_TC_BF16]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    M.build()
+    yield
+
+
+def rel_rows(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def run(x, form, direction=M.FFT_FORWARD, adjoint=False, rows=None):
+    batch, n = x.shape
+    d_in = torch.from_numpy(x).to(torch.complex64).cuda()
+    d_out = torch.empty_like(d_in)
+    p = M.fft_plan_ex(n, batch, M.FFT_C64, direction, form)
+    try:
+        (M.fft_exec_adjoint if adjoint else M.fft_exec)(p, d_in, d_out)
+        M.fft_plan_check(p)  # raises on a recorded mbarrier timeout
+        desc = M.fft_plan_describe(p)
+    finally:
+        M.fft_destroy(p)
+    assert '"form": "tc_' in desc
+    out = d_out if rows is None else d_out[rows]
+    return out.cpu().numpy().astype(np.complex128)
+
+
+def c64(x):
+    return x.astype(np.complex64).astype(np.complex128)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("t", [6, 7, 8, 9, 10, 11, 12, 13, 14, 16])
+def test_tc_sizes(form, t):
+    n = 1 << t
+    x = W.gaussian_complex(n, 3, seed=t)
+    ref_in = c64(x)
+    for direction, op in ((M.FFT_FORWARD, "forward"), (M.FFT_INVERSE, "inverse")):
+        y = run(x, form, direction)
+        err = rel_rows(y, O.fft(ref_in, op, c=256))
+        assert err.max() <= 1e-5 * t, (t, op, err.max())
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_tc_adjoint(form):
+    n = 1 << 12
+    x = W.gaussian_complex(n, 2, seed=5)
+    y = run(x, form, M.FFT_FORWARD, adjoint=True)
+    assert rel_rows(y, O.fft(c64(x), "adjoint_forward", c=256)).max() <= 1e-5 * 12
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("kind", ["gaussian", "dynamic_range"])
+def test_tc_precision_config(form, kind):
+    """complex64 n = 2^16, batch 4096; Gaussian sigma = 1 and amplitudes
+    log-uniform over 1e-4 .. 1e4; sampled transforms against the oracle."""
+    n, batch = 1 << 16, 4096
+    gen = W.gaussian_complex if kind == "gaussian" else W.dynamic_range_complex
+    x = gen(n, batch, seed=0)
+    picks = [0, 2049, batch - 1]
+    y = run(x, form, rows=picks)
+    ref = O.fft(c64(x[picks]), "forward", c=1024, threads=3)
+    err = rel_rows(y, ref)
+    assert err.max() <= 1e-5 * 16, err
