@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
+    ap.add_argument("--extra", action="store_true",
+                    help="also measure the other configurations (latency, precision forms, uneven "
+                         "batch, forward+adjoint); one JSON line each on stderr")
     return ap.parse_args()
 
 
@@ -339,6 +342,8 @@ def run_moafft(args):
 
     for t in [int(v) for v in args.sweep.split(",") if v.strip()]:
         sweep_line(M, torch, dev, stream, t, args)
+    if args.extra and rank == 0:
+        extra_configs(M, torch, dev, stream)
 
     fwd.close()
     inv.close()
@@ -404,6 +409,126 @@ def sweep_line(M, torch, dev, stream, log2n, args):
           file=sys.stderr, flush=True)
     fwd.close()
     inv.close()
+
+
+def _time(torch, stream, fn, reps, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _emit(d):
+    print(json.dumps(d), file=sys.stderr, flush=True)
+
+
+def extra_configs(M, torch, dev, stream):
+    """The remaining configurations, measured on the same GPU.  Errors are
+    relative L2 against the library's own FP64 (complex128) path, which the
+    test-suite checks against the oracle."""
+    import numpy as np
+    import workloads as W
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = json.load(f)["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+
+    def rel(a, b):
+        return (torch.linalg.vector_norm((a.to(torch.complex128) - b).flatten()) /
+                torch.linalg.vector_norm(b.flatten())).item()
+
+    # latency: complex128 n = 2^10, batch 1
+    n = 1 << 10
+    x = torch.from_numpy(W.uniform_complex(n, 1, seed=0)).to(dev)
+    y = torch.empty_like(x)
+    p = M.Plan(n, 1, M.FFT_C128, M.FFT_FORWARD)
+    ms = _time(torch, stream, lambda: p.exec(x, y, stream), 200)
+    M.fft_plan_profile(p.handle, True)
+    for _ in range(50):
+        p.exec(x, y, stream)
+    kt = M.fft_plan_pass_times(p.handle)
+    kms = sum(t for t, _ in kt) / 50
+    _emit({"config": "c128 n=2^10 batch 1 forward", "us_per_call_host_bound": round(ms * 1e3, 3),
+           "us_kernel": round(kms * 1e3, 3), "gflops_kernel": round(5 * n * 10 / (kms * 1e-3) / 1e9, 3)})
+    p.close()
+
+    # precision forms: complex64 n = 2^16, batch 4096 (Gaussian sigma = 1)
+    n, batch = 1 << 16, 4096
+    xc = torch.randn(batch, n, dtype=torch.complex64, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    ref = torch.empty(batch, n, dtype=torch.complex128, device=dev)
+    p64 = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD)
+    x128 = xc.to(torch.complex128)
+    ms64 = _time(torch, stream, lambda: p64.exec(x128, ref, stream), 3)
+    del x128
+    p64.close()
+    fl = 5.0 * n * 16 * batch
+    _emit({"config": "c128 FP64 plain n=2^16 batch 4096 forward", "ms": round(ms64, 3),
+           "gflops": round(fl / (ms64 * 1e-3) / 1e9, 1)})
+    out = torch.empty_like(xc)
+    for form, name in ((M.FFT_FORM_PLAIN, "FP32 plain"), (M.FFT_FORM_TC_FP16, "TC split FP16"),
+                       (M.FFT_FORM_TC_BF16, "TC split BF16")):
+        pf = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form)
+        ms = _time(torch, stream, lambda: pf.exec(xc, out, stream), 5)
+        M.fft_plan_check(pf.handle)
+        gbs = 2 * n * batch * 8 / (ms * 1e-3) / 1e9
+        _emit({"config": f"c64 {name} n=2^16 batch 4096 forward", "ms": round(ms, 3),
+               "gflops": round(fl / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
+               "hbm_frac_of_measured": round(gbs / hbm, 4) if hbm else None,
+               "rel_err_vs_fp64": rel(out, ref), "speedup_vs_fp64": round(ms64 / ms, 2)})
+        pf.close()
+    del ref, out, xc
+
+    # uneven batch: 20,000 complex64 transforms, n in 2^6..2^16 (seed 1)
+    sizes, data = W.uneven_batch()
+    xu = torch.from_numpy(data).to(torch.complex64).to(dev)
+    yu = torch.empty_like(xu)
+    pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
+    ms_g = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
+    launches = M.fft_plan_launches(pm)
+    M.fft_destroy(pm)
+    plans = {}
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+
+    def per_transform():
+        for s_, o in zip(sizes.tolist(), offs.tolist()):
+            if s_ not in plans:
+                plans[s_] = M.fft_plan(s_, 1, M.FFT_C64, M.FFT_FORWARD)
+            M.fft_exec(plans[s_], xu[o:o + s_], yu[o:o + s_], stream)
+
+    ms_p = _time(torch, stream, per_transform, 1, warm=1)
+    for h in plans.values():
+        M.fft_destroy(h)
+    fl = float(sum(5 * s_ * np.log2(s_) for s_ in sizes.tolist()))
+    _emit({"config": "c64 uneven batch 20000 transforms n=2^6..2^16", "graph_ms": round(ms_g, 3),
+           "graph_launches": launches, "graph_gflops": round(fl / (ms_g * 1e-3) / 1e9, 1),
+           "per_transform_launch_ms": round(ms_p, 3), "speedup": round(ms_p / ms_g, 1)})
+    del xu, yu
+
+    # differentiation: complex64 n = 2^18, batch 256, forward + adjoint
+    n, batch = 1 << 18, 256
+    xd = torch.randn(batch, n, dtype=torch.complex64, device=dev)
+    yd = torch.empty_like(xd)
+    gd = torch.empty_like(xd)
+    pd = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD)
+
+    def fwd_adj():
+        pd.exec(xd, yd, stream)
+        pd.exec_adjoint(yd, gd, stream)
+
+    ms = _time(torch, stream, fwd_adj, 5)
+    _emit({"config": "c64 n=2^18 batch 256 forward + adjoint", "ms": round(ms, 3),
+           "gflops": round(2 * 5.0 * n * 18 * batch / (ms * 1e-3) / 1e9, 1),
+           "gbs": round(4 * n * batch * 8 / (ms * 1e-3) / 1e9, 1)})
+    pd.close()
 
 
 def main():

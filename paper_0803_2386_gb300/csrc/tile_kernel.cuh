@@ -46,6 +46,7 @@ template <typename T>
 __host__ __device__ constexpr int tile_min_blocks(int logr)
 {
     // c128: two 256-thread CTAs per SM (<= 128 registers); c64: three
+    // (four, with a 64-register cap, spills and measured slower)
     return (sizeof(T) == 8 ? 512 : 768) / tile_threads(logr) > 32
                ? 32
                : (sizeof(T) == 8 ? 512 : 768) / tile_threads(logr);
