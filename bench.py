@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
+    ap.add_argument("--case", default="", choices=["", "c64", "tc_fp16", "tc_bf16"],
+                    help="small profiling case: complex64 n=2^16 batch 512 forward, three runs")
     ap.add_argument("--extra", action="store_true",
                     help="also measure the other configurations (latency, precision forms, uneven "
                          "batch, forward+adjoint); one JSON line each on stderr")
@@ -282,11 +284,7 @@ def run_moafft(args):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    t_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = t.item()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = t_ms / args.steps
     value = flops_per_step(n, batch) * world / (ms_step * 1e-3) / 1e9
     launches = args.steps * (fwd.launches + inv.launches)
@@ -369,11 +367,7 @@ def measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, wor
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
     rt_host = float((torch.linalg.vector_norm(yh - xh) / torch.linalg.vector_norm(xh)).item())
     bytes_buf = n * batch * 16
     e2e = {"value": round(flops_per_step(n, batch) * world / e2e_s / 1e9, 3), "unit": UNIT,
@@ -531,8 +525,37 @@ def extra_configs(M, torch, dev, stream):
     pd.close()
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the job's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_case(args):
+    """A small case for ncu captures of the complex64 kernels."""
+    import torch
+    import paper_0803_2386_gb300 as M
+    form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16}[args.case]
+    n, batch = 1 << 16, 512
+    x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form, "8,8;chunk=512")
+    for _ in range(3):
+        p.exec(x, y)
+    M.fft_plan_check(p.handle)
+    p.close()
+    print("ok")
+    return 0
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_moafft(args)

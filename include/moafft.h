@@ -198,6 +198,16 @@ typedef void *(*fft_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*fft_free_fn)(void *ptr, void *ctx);
 int fft_set_allocator(fft_alloc_fn alloc, fft_free_fn release, void *ctx);
 
+/* The autotuner's search space for length n: a JSON list of the schedule
+ * strings "auto" times (pass radix splits, each with workspace-round
+ * variants).  Host logic only.  The winner is appended to the cache file
+ * named by $MOAFFT_TUNE_CACHE (default $HOME/.cache/moafft_tune.jsonl), keyed
+ * by GPU name, n, batch (power-of-two bucket), dtype and form; plans created
+ * with a NULL or "" schedule, and the size classes of fft_plan_many, use a
+ * cached winner when there is one.  Cite: Ch.2 (block size chosen at run
+ * time) and Table 4 (the radix sweep). */
+int fft_tune_candidates(int64_t n, fft_dtype dt, fft_form form, char *buf, int64_t len);
+
 /* Library version as 10000*major + 100*minor + patch. */
 int fft_version(void);
 

@@ -41,7 +41,7 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
 # every symbol include/moafft.h declares
 EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_exec", "fft_exec_adjoint",
            "fft_exec_host", "fft_exec_noalloc", "fft_plan_check", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
-           "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_version"]
+           "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_tune_candidates", "fft_version"]
 
 _LIB = None
 
@@ -90,6 +90,7 @@ def lib():
             "fft_plan_launches": (i64, [vp]),
             "fft_plan_workspace_bytes": (i64, [vp]),
             "fft_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+            "fft_tune_candidates": (i32, [i64, i32, i32, ctypes.c_char_p, i64]),
             "fft_version": (i32, []),
         }
         for name, (res, args) in sig.items():
@@ -244,6 +245,13 @@ def fft_set_allocator(alloc=None, release=None, ctx=None):
     f = FREE_FN(lambda p, _c: release(p))
     _ALLOC_KEEP[:] = [a, f]
     _check(lib().fft_set_allocator(a, f, ctx))
+
+
+def fft_tune_candidates(n: int, dtype: int = FFT_C64, form: int = FFT_FORM_PLAIN) -> list:
+    import json
+    buf = ctypes.create_string_buffer(65536)
+    _check(lib().fft_tune_candidates(n, dtype, form, buf, len(buf)))
+    return json.loads(buf.value.decode())
 
 
 def fft_version() -> int:

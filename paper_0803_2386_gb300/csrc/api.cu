@@ -19,6 +19,9 @@
 #include <string>
 #include <vector>
 
+#include <sys/stat.h>
+#include <cmath>
+
 #include "internal.h"
 
 using namespace moafft;
@@ -258,6 +261,111 @@ static std::string schedule_json(const Schedule &s)
     return j;
 }
 
+
+// ------------------------------------------------------------ autotuner ---
+//
+// The paper leaves the block size c to the user at run time so that each
+// machine can use its best one (Ch.2, "specify the blocking size at run
+// time"; Table 4 sweeps the radix).  Here the choice is searched: candidate
+// pass schedules (how log2 n splits into HBM passes, and how many transforms
+// a workspace round holds) are timed on the GPU and the fastest is cached.
+
+static std::vector<std::string> tune_candidates(int64_t n, fft_dtype dt)
+{
+    std::vector<std::string> out;
+    const int t = exact_log2(n);
+    if (t <= 12) {
+        out.push_back(std::to_string(t));
+        if (t >= 8)
+            for (int r0 = 4; r0 <= t - 4; r0++) out.push_back(std::to_string(r0) + "," + std::to_string(t - r0));
+        return out;
+    }
+    for (int r0 = 4; r0 <= 12; r0++) {
+        const int r1 = t - r0;
+        if (r1 >= 4 && r1 <= 12) out.push_back(std::to_string(r0) + "," + std::to_string(r1));
+    }
+    for (int r0 = 4; r0 <= 12; r0++)
+        for (int r1 = 4; r1 <= 12; r1++) {
+            const int r2 = t - r0 - r1;
+            if (r2 >= 4 && r2 <= 12 && std::abs(r0 - r1) <= 2 && std::abs(r1 - r2) <= 2)
+                out.push_back(std::to_string(r0) + "," + std::to_string(r1) + "," + std::to_string(r2));
+        }
+    // workspace-round variants of the default-like splits
+    std::vector<std::string> with_chunks;
+    for (const auto &c : out) {
+        with_chunks.push_back(c);
+        const int64_t eb = dt == FFT_C128 ? 16 : 8;
+        for (int64_t mb : {64, 1024}) {
+            const int64_t ch = std::max<int64_t>(1, (mb << 20) / (n * eb));
+            with_chunks.push_back(c + ";chunk=" + std::to_string(ch));
+        }
+    }
+    return with_chunks;
+}
+
+static std::string tune_cache_path()
+{
+    const char *env = getenv("MOAFFT_TUNE_CACHE");
+    if (env && *env) return env;
+    const char *home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/moafft_tune.jsonl";
+}
+
+static std::string tune_key(int64_t n, int64_t batch, fft_dtype dt, fft_form form)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) gpu = prop.name;
+    else cudaGetLastError();
+    // batch is bucketed by its power of two: the best schedule depends on how
+    // full the GPU is, not on the exact count
+    int bb = 0;
+    while (((int64_t)1 << (bb + 1)) <= batch) bb++;
+    return gpu + "|n=" + std::to_string(n) + "|b=2^" + std::to_string(bb) + "|" + (dt == FFT_C128 ? "c128" : "c64") +
+           "|form=" + std::to_string((int)form);
+}
+
+static std::string tune_lookup(const std::string &key)
+{
+    FILE *f = fopen(tune_cache_path().c_str(), "r");
+    if (!f) return "";
+    std::string best;
+    char line[1024];
+    const std::string k = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        if (l.find(k) == std::string::npos) continue;
+        size_t a = l.find("\"schedule\": \"");
+        if (a == std::string::npos) continue;
+        a += 13;
+        size_t b = l.find('"', a);
+        if (b != std::string::npos) best = l.substr(a, b - a);  // the last entry wins
+    }
+    fclose(f);
+    return best;
+}
+
+static void tune_store(const std::string &key, const std::string &sched, double ms)
+{
+    const std::string path = tune_cache_path();
+    size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        std::string dir = path.substr(0, slash);
+        std::string cmd;  // create the directory without a shell
+        for (size_t i = 1; i <= dir.size(); i++)
+            if (i == dir.size() || dir[i] == '/') {
+                std::string sub = dir.substr(0, i);
+                mkdir(sub.c_str(), 0755);
+            }
+    }
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"schedule\": \"%s\", \"ms\": %.6f}\n", key.c_str(), sched.c_str(), ms);
+    fclose(f);
+}
+
 // ---------------------------------------------------------------- plans ---
 
 // One length of the batch: a plain plan has one class (dense layout); an
@@ -481,6 +589,9 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
     return make_tables(p);
 }
 
+static int autotune(int64_t n, int64_t batch, fft_dtype dt, fft_dir dir, fft_form form, std::string &best);
+static int put(char *buf, int64_t len, const std::string &s);
+
 extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,
                            fft_form form, const char *schedule)
 {
@@ -493,6 +604,14 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
         return fail(FFT_ERR_ARG, "unknown form %d", (int)form);
     if (form != FFT_FORM_PLAIN && dt != FFT_C64)
         return fail(FFT_ERR_UNSUPPORTED, "the tensor-core forms take complex64 data");
+    std::string chosen = schedule ? schedule : "";
+    if (chosen == "auto") {
+        int st2 = autotune(n, batch, dt, dir, form, chosen);
+        if (st2 != FFT_OK) return st2;
+    } else if (chosen.empty()) {
+        chosen = tune_lookup(tune_key(n, batch, dt, form));  // "" when not tuned yet
+    }
+    schedule = chosen.c_str();
     fft_plan_s *p = new (std::nothrow) fft_plan_s();
     if (!p) return fail(FFT_ERR_ALLOC, "host allocation of the plan failed");
     p->n = n;
@@ -558,7 +677,11 @@ extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t coun
               [](const SizeClass &a, const SizeClass &b) { return a.n < b.n; });
     int st = FFT_OK;
     for (auto &c : p->classes) {
-        st = build_schedule(c.sched, c.n, dt, nullptr, nullptr);
+        // a tuned schedule for this length and class size, if one is cached
+        std::string tuned = tune_lookup(tune_key(c.n, c.count, dt, FFT_FORM_PLAIN));
+        size_t semi = tuned.find(';');
+        if (semi != std::string::npos) tuned = tuned.substr(0, semi);  // rounds are per class here
+        st = build_schedule(c.sched, c.n, dt, tuned.c_str(), nullptr);
         if (st != FFT_OK) break;
     }
     if (st == FFT_OK) st = finish_plan(p, 0);
@@ -894,6 +1017,66 @@ extern "C" int fft_plan_pass_times(fft_plan_t p, double *ms, int64_t *launches, 
     int np = 0;
     for (const auto &c : p->classes) np = std::max(np, c.sched.npass);
     return p->use_graph ? 1 : np;
+}
+
+
+// Time every candidate on a batch large enough to fill the GPU (up to 2^24
+// points), keep the fastest, append it to the cache.
+static int autotune(int64_t n, int64_t batch, fft_dtype dt, fft_dir dir, fft_form form, std::string &best)
+{
+    const size_t eb = elem_bytes(dt);
+    const int64_t tb = std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)1 << 24) / n));
+    DevBuf bin, bout;
+    int st = dev_alloc(bin, (size_t)(tb * n) * eb, "autotune input");
+    if (st == FFT_OK) st = dev_alloc(bout, (size_t)(tb * n) * eb, "autotune output");
+    if (st != FFT_OK) {
+        dev_free(bin);
+        return st;
+    }
+    cudaMemset(bin.ptr, 0, (size_t)(tb * n) * eb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e30;
+    best.clear();
+    for (const auto &cand : tune_candidates(n, dt)) {
+        fft_plan_t p = nullptr;
+        if (fft_plan_ex(&p, n, tb, dt, dir, form, cand.c_str()) != FFT_OK) continue;
+        bool ok = fft_exec(p, bin.ptr, bout.ptr, nullptr) == FFT_OK;
+        if (ok) {
+            cudaEventRecord(e0, 0);
+            for (int r = 0; r < 3 && ok; r++) ok = fft_exec(p, bin.ptr, bout.ptr, nullptr) == FFT_OK;
+            cudaEventRecord(e1, 0);
+        }
+        float ms = 0.f;
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            if (ms / 3 < best_ms) {
+                best_ms = ms / 3;
+                best = cand;
+            }
+        }
+        cudaGetLastError();
+        fft_destroy(p);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(bin);
+    dev_free(bout);
+    if (best.empty()) return fail(FFT_ERR_CUDA, "autotune: no candidate schedule ran");
+    tune_store(tune_key(n, batch, dt, form), best, best_ms);
+    return FFT_OK;
+}
+
+extern "C" int fft_tune_candidates(int64_t n, fft_dtype dt, fft_form form, char *buf, int64_t len)
+{
+    int st = check_common(n, dt, FFT_FORWARD);
+    if (st != FFT_OK) return st;
+    (void)form;
+    std::string j = "[";
+    auto c = tune_candidates(n, dt);
+    for (size_t i = 0; i < c.size(); i++) j += (i ? ", \"" : "\"") + c[i] + "\"";
+    j += "]";
+    return put(buf, len, j);
 }
 
 // --------------------------------------------------------- introspection --

@@ -119,3 +119,14 @@ def test_allocator_hook_arguments():
         M.lib().fft_set_allocator(M.ALLOC_FN(lambda n, c: 0), M.FREE_FN(), None) and None
         _ = M._check(M.lib().fft_set_allocator(M.ALLOC_FN(lambda n, c: 0), M.FREE_FN(), None))
     M.fft_set_allocator(None, None)
+
+
+@pytest.mark.parametrize("t", [0, 3, 6, 10, 12, 13, 16, 20, 24])
+@pytest.mark.parametrize("dt", [M.FFT_C64, M.FFT_C128])
+def test_tune_candidates_are_valid_schedules(t, dt):
+    """Every schedule the autotuner may time covers all log2 n stages."""
+    cands = M.fft_tune_candidates(1 << t, dt)
+    assert cands and len(set(cands)) == len(cands)
+    for c in cands:
+        s = json.loads(M.fft_describe_schedule(1 << t, dt, M.FFT_FORM_PLAIN, c))
+        assert sum(p["log_r"] for p in s["passes"]) == t
