@@ -390,6 +390,7 @@ struct fft_plan_s {
     DevBuf tw;   // twiddle arena
     DevBuf ws;   // inter-pass workspace
     DevBuf err;  // int set by a kernel whose bounded wait gave up
+    DevBuf tcf;  // tensor-core form: split DFT matrices for both directions
     int64_t ws_bytes = 0;
     int device = 0;
     // kernel timing (fft_plan_profile)
@@ -528,6 +529,7 @@ static void destroy_plan(fft_plan_s *p)
     dev_free(p->ws);
     dev_free(p->tw);
     dev_free(p->err);
+    dev_free(p->tcf);
     for (auto &c : p->classes) dev_free(c.d_off);
     for (int k = 0; k < 2; k++) {
         dev_free(p->stage_in[k]);
@@ -586,6 +588,12 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
     if (st != FFT_OK) return st;
     e = cudaMemset(p->err.ptr, 0, sizeof(int));
     if (e != cudaSuccess) return fail_cuda(e, "error word");
+    if (p->form != FFT_FORM_PLAIN) {
+        st = dev_alloc(p->tcf, 8192, "tensor-core DFT matrices");
+        if (st != FFT_OK) return st;
+        e = launch_tc_tables(p->tcf.ptr, p->form == FFT_FORM_TC_BF16, 0);
+        if (e != cudaSuccess) return fail_cuda(e, "tensor-core DFT matrices");
+    }
     return make_tables(p);
 }
 
@@ -761,6 +769,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.tw_lo_bits = d.tw_lo_bits;
             a.scale = a.is_last ? scale : 1.0;
             a.err = (int *)p->err.ptr;
+            a.tc_dft = p->tcf.ptr ? (const char *)p->tcf.ptr + (sign < 0 ? 0 : 4096) : nullptr;
             fft_plan_s::Rec rec{i, nullptr, nullptr};
             if (p->profile) {
                 rec.a = take_event(p);

@@ -66,6 +66,9 @@ struct PassArgs {
     const int64_t *out_off;
     // device word set to 1 when a bounded wait inside a kernel gave up
     int *err;
+    // tensor-core form: the split 32x32 DFT matrix of this direction, hi
+    // then lo, 2 x 2048 bytes in the K-major core-matrix layout
+    const void *tc_dft;
 };
 
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
@@ -74,6 +77,9 @@ cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);
 // tensor-core radix-16 form (tc_f32.cu); returns cudaErrorNotSupported when
 // the pass is not a tile it covers
 bool tc_covers(const PassArgs &a);
+// writes the split DFT matrices for both directions (dir -1 first, then +1),
+// 4096 bytes each, into dst (tc_f32.cu)
+cudaError_t launch_tc_tables(void *dst, bool bf16, cudaStream_t s);
 cudaError_t launch_tc_f32(const PassArgs &a, int dir, bool bf16, cudaStream_t s);
 
 // twiddle generation (twiddle.cu): dst[j] = exp(-2*pi*i * j*stride / m),

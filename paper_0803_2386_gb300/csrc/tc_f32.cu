@@ -47,6 +47,13 @@ static cudaError_t launch_tc_dir(const PassArgs &a, cudaStream_t s)
     }
 }
 
+cudaError_t launch_tc_tables(void *dst, bool bf16, cudaStream_t s)
+{
+    if (bf16) tc_dft_tables_kernel<true><<<8, 256, 0, s>>>(reinterpret_cast<unsigned char *>(dst));
+    else tc_dft_tables_kernel<false><<<8, 256, 0, s>>>(reinterpret_cast<unsigned char *>(dst));
+    return cudaGetLastError();
+}
+
 bool tc_covers(const PassArgs &a) { return a.log_r >= 6 && a.log_r <= 12 && tile_covers(a); }
 
 cudaError_t launch_tc_f32(const PassArgs &a, int dir, bool bf16, cudaStream_t s)

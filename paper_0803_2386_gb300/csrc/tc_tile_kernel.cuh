@@ -127,6 +127,28 @@ __device__ __forceinline__ void tc_dft16(float2 *v, TcState &st, int *err)
     tc::fence_before_sync();
 }
 
+// F^T (row = output real index n = 2k + b, column = input real index
+// k = 2e + a) split into hi and lo 16-bit parts, K-major core-matrix layout;
+// dst holds [dir -1: hi, lo][dir +1: hi, lo], 2048 bytes each.
+template <bool BF16>
+__global__ void tc_dft_tables_kernel(unsigned char *dst)
+{
+    using H = Half16<BF16>;
+    for (int q = threadIdx.x + blockIdx.x * blockDim.x; q < 2 * 32 * 32; q += blockDim.x * gridDim.x) {
+        const int d = q >> 10, nrow = (q >> 5) & 31, k = q & 31;
+        const int dir = d == 0 ? -1 : 1;
+        const int kp = nrow >> 1, bb = nrow & 1, ee = k >> 1, aa = k & 1;
+        double sn, cs;
+        sincospi((double)dir * 2.0 * (double)((ee * kp) & 15) / 16.0, &sn, &cs);
+        const double f = aa == 0 ? (bb == 0 ? cs : sn) : (bb == 0 ? -sn : cs);
+        const typename H::T hi = H::rn((float)f);
+        const typename H::T lo = H::rn((float)(f - (double)H::f(hi)));
+        unsigned char *base = dst + d * 4096;
+        *reinterpret_cast<typename H::T *>(base + tc::kmajor_off(nrow, k)) = hi;
+        *reinterpret_cast<typename H::T *>(base + 2048 + tc::kmajor_off(nrow, k)) = lo;
+    }
+}
+
 template <int DIR, int LOGR>
 __host__ __device__ constexpr size_t tc_smem_bytes()
 {
@@ -218,18 +240,12 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) tc_tile_kernel(PassArgs
     }
     const int64_t mstride = LAST ? 1 : p.B;
 
-    // ---- the split DFT matrix F (as F^T, K-major: row = output real index)
-    for (int q = tid; q < 32 * 32; q += NT) {
-        const int nrow = q >> 5, k = q & 31;
-        const int kp = nrow >> 1, bb = nrow & 1, ee = k >> 1, aa = k & 1;
-        double sn, cs;
-        sincospi((double)DIR * 2.0 * (double)((ee * kp) & 15) / 16.0, &sn, &cs);
-        const double f = aa == 0 ? (bb == 0 ? cs : sn) : (bb == 0 ? -sn : cs);
-        using H = Half16<BF16>;
-        const typename H::T hi = H::rn((float)f);
-        const typename H::T lo = H::rn((float)(f - (double)H::f(hi)));
-        *reinterpret_cast<typename H::T *>(b_hi + tc::kmajor_off(nrow, k)) = hi;
-        *reinterpret_cast<typename H::T *>(b_lo + tc::kmajor_off(nrow, k)) = lo;
+    // ---- the split DFT matrix F of this direction (made once per plan):
+    // 4 KB copied into shared memory, hi then lo
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.tc_dft);
+        uint4 *dst = reinterpret_cast<uint4 *>(b_hi);  // b_lo follows b_hi contiguously
+        for (int q = tid; q < 4096 / 16; q += NT) dst[q] = __ldg(src + q);
     }
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (tid < 32) tc::tmem_alloc(&tmem_slot, (uint32_t)(NT / 128 * 32 < 32 ? 32 : NT / 128 * 32));
