@@ -486,6 +486,13 @@ def extra_configs(M, torch, dev, stream):
     xu = torch.from_numpy(data).to(torch.complex64).to(dev)
     yu = torch.empty_like(xu)
     pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
+    ms_pers = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
+    M.fft_plan_check(pm)
+    pers = json.loads(M.fft_plan_describe(pm))["persistent"]
+    M.fft_destroy(pm)
+    os.environ["MOAFFT_NO_PERSIST"] = "1"
+    pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
+    del os.environ["MOAFFT_NO_PERSIST"]
     ms_g = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
     launches = M.fft_plan_launches(pm)
     M.fft_destroy(pm)
@@ -502,7 +509,9 @@ def extra_configs(M, torch, dev, stream):
     for h in plans.values():
         M.fft_destroy(h)
     fl = float(sum(5 * s_ * np.log2(s_) for s_ in sizes.tolist()))
-    _emit({"config": "c64 uneven batch 20000 transforms n=2^6..2^16", "graph_ms": round(ms_g, 3),
+    _emit({"config": "c64 uneven batch 20000 transforms n=2^6..2^16",
+           "persistent_ms": round(ms_pers, 3), "persistent": pers,
+           "persistent_gflops": round(fl / (ms_pers * 1e-3) / 1e9, 1), "graph_ms": round(ms_g, 3),
            "graph_launches": launches, "graph_gflops": round(fl / (ms_g * 1e-3) / 1e9, 1),
            "per_transform_launch_ms": round(ms_p, 3), "speedup": round(ms_p / ms_g, 1)})
     del xu, yu

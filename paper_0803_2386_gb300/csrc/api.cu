@@ -409,6 +409,11 @@ struct fft_plan_s {
                 ev_d2h[2] = {nullptr, nullptr};
     // uneven plans replay one captured graph per (in, out, adjoint)
     bool use_graph = false;
+    // ... whose body is one persistent kernel when every class fits it
+    bool persist = false;
+    std::vector<int64_t> ws_off;  // per class: element offset of its workspace
+    int n_ctr = 0;
+    DevBuf d_segs, d_queue, d_ctr;
     cudaStream_t s_capture = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void *g_in = nullptr;
@@ -459,6 +464,7 @@ static int64_t class_launches(const SizeClass &c)
 
 static int64_t launches_per_exec(const fft_plan_s *p)
 {
+    if (p->persist) return 1;
     int64_t k = 0;
     for (const auto &c : p->classes) k += class_launches(c);
     return k;
@@ -530,6 +536,9 @@ static void destroy_plan(fft_plan_s *p)
     dev_free(p->tw);
     dev_free(p->err);
     dev_free(p->tcf);
+    dev_free(p->d_segs);
+    dev_free(p->d_queue);
+    dev_free(p->d_ctr);
     for (auto &c : p->classes) dev_free(c.d_off);
     for (int k = 0; k < 2; k++) {
         dev_free(p->stage_in[k]);
@@ -648,6 +657,147 @@ extern "C" int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt,
     return fft_plan_ex(out, n, batch, dt, dir, FFT_FORM_PLAIN, nullptr);
 }
 
+// tiles a pass launches for `count` transforms at width W
+static int64_t pass_ctas(const PassDesc &d, int64_t count)
+{
+    const int64_t W = d.width;
+    if (d.B > 1) return count * d.A * (d.B / W);
+    if (d.A > 1) return count * (d.A / W);
+    return (count + W - 1) / W;
+}
+
+static int persist_width_host(int logr) { return 4096 >> logr; }
+
+// Switch an uneven plan to the persistent kernel when every class has one or
+// two passes of 2^4..2^12 points that the 256-thread tiles can cover.
+static int try_persist(fft_plan_s *p)
+{
+    size_t eb = elem_bytes(p->dt);
+    for (auto &c : p->classes) {
+        if (c.sched.npass > 2) return FFT_OK;
+        for (int i = 0; i < c.sched.npass; i++) {
+            PassDesc &d = c.sched.pass[i];
+            if (d.log_r < 4 || d.log_r > 12) return FFT_OK;
+            const int64_t W = persist_width_host(d.log_r);
+            const bool last = i == c.sched.npass - 1;
+            if (!last && (d.B < W || d.B % W)) return FFT_OK;
+            if (last && d.A > 1 && (d.A < W || d.A % W)) return FFT_OK;
+        }
+    }
+    int64_t ws = 0;
+    p->ws_off.assign(p->classes.size(), 0);
+    p->n_ctr = 0;
+    for (size_t k = 0; k < p->classes.size(); k++) {
+        SizeClass &c = p->classes[k];
+        for (int i = 0; i < c.sched.npass; i++) c.sched.pass[i].width = persist_width_host(c.sched.pass[i].log_r);
+        if (c.sched.npass == 2) {
+            // one region per class: no round waits for another round's slot
+            // (a two-slot ring measured slower: the extra waits serialise the
+            // rounds)
+            p->ws_off[k] = ws;
+            ws += c.count * c.n;
+            p->n_ctr += (int)((c.count + c.chunk - 1) / c.chunk);
+        }
+    }
+    dev_free(p->ws);
+    p->ws_bytes = ws * (int64_t)eb;
+    int st = ws ? dev_alloc(p->ws, (size_t)p->ws_bytes, "workspace") : FFT_OK;
+    if (st == FFT_OK) st = dev_alloc(p->d_queue, sizeof(unsigned long long), "ticket counter");
+    if (st == FFT_OK) st = dev_alloc(p->d_ctr, sizeof(int) * (size_t)std::max(1, p->n_ctr), "round counters");
+    if (st != FFT_OK) return st;
+    p->persist = true;
+    return FFT_OK;
+}
+
+static void fill_args(const fft_plan_s *p, const SizeClass &C, int i, PassArgs &a)
+{
+    size_t eb = elem_bytes(p->dt);
+    const PassDesc &d = C.sched.pass[i];
+    memset(&a, 0, sizeof a);
+    a.n = C.n;
+    a.npass = C.sched.npass;
+    for (int k = 0; k < C.sched.npass; k++) a.pass_log[k] = C.sched.pass[k].log_r;
+    a.log_r = d.log_r;
+    a.width = d.width;
+    a.nsub = d.nsub;
+    for (int k = 0; k < kMaxSub; k++) a.sub_log[k] = d.sub_log[k];
+    a.A = d.A;
+    a.B = d.B;
+    a.is_last = (i == C.sched.npass - 1);
+    a.tw_tile = (const char *)p->tw.ptr + d.tw_tile_off * eb;
+    a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
+    a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
+    a.tw_lo_bits = d.tw_lo_bits;
+    a.scale = a.is_last && p->dir == FFT_INVERSE ? 1.0 / (double)C.n : 1.0;
+    a.err = (int *)p->err.ptr;
+}
+
+// The persistent launch's segments for buffers (in, out): single-pass
+// classes first, then per two-pass class its rounds in the order
+// p0(0), p0(1), p1(0), p0(2), p1(1), ..., p1(K-1).
+static void build_segments(const fft_plan_s *p, const void *in, void *out, std::vector<PersistSeg> &segs,
+                           long long &total)
+{
+    size_t eb = elem_bytes(p->dt);
+    segs.clear();
+    total = 0;
+    auto add = [&](const PassArgs &a, const PassDesc &d, int64_t count, int wait, int target, int signal) {
+        PersistSeg g;
+        g.a = a;
+        g.a.count = count;
+        g.first = total;
+        g.nctas = pass_ctas(d, count);
+        g.wait_ctr = wait;
+        g.wait_target = target;
+        g.signal_ctr = signal;
+        g.log_r = d.log_r;
+        g.last = a.is_last;
+        total += g.nctas;
+        segs.push_back(g);
+    };
+    for (const auto &c : p->classes) {
+        if (c.sched.npass != 1) continue;
+        PassArgs a;
+        fill_args(p, c, 0, a);
+        a.in = in;
+        a.out = out;
+        a.in_off = a.out_off = (const int64_t *)c.d_off.ptr;
+        add(a, c.sched.pass[0], c.count, -1, 0, -1);
+    }
+    int ctr = 0;
+    for (size_t k = 0; k < p->classes.size(); k++) {
+        const SizeClass &c = p->classes[k];
+        if (c.sched.npass != 2) continue;
+        const int64_t K = (c.count + c.chunk - 1) / c.chunk;
+        // counter ctr + j counts the finished first-pass tiles of round j
+        auto round = [&](int pass, int64_t j) {
+            const int64_t t0 = j * c.chunk, cnt = std::min(c.chunk, c.count - t0);
+            char *ws = (char *)p->ws.ptr + (size_t)(p->ws_off[k] + t0 * c.n) * eb;
+            PassArgs a;
+            fill_args(p, c, pass, a);
+            const int64_t *off = (const int64_t *)c.d_off.ptr + t0;
+            if (pass == 0) {
+                a.in = in;
+                a.in_off = off;
+                a.out = ws;
+                add(a, c.sched.pass[0], cnt, -1, 0, ctr + (int)j);
+            } else {
+                a.in = ws;
+                a.out = out;
+                a.out_off = off;
+                add(a, c.sched.pass[1], cnt, ctr + (int)j, (int)pass_ctas(c.sched.pass[0], cnt), -1);
+            }
+        };
+        round(0, 0);
+        for (int64_t j = 1; j < K; j++) {
+            round(0, j);
+            round(1, j - 1);
+        }
+        round(1, K - 1);
+        ctr += (int)K;
+    }
+}
+
 extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t count, fft_dtype dt,
                              fft_dir dir)
 {
@@ -693,6 +843,7 @@ extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t coun
         if (st != FFT_OK) break;
     }
     if (st == FFT_OK) st = finish_plan(p, 0);
+    if (st == FFT_OK && !getenv("MOAFFT_NO_PERSIST")) st = try_persist(p);
     if (st != FFT_OK) {
         destroy_plan(p);
         return st;
@@ -812,11 +963,35 @@ static int exec_graph(fft_plan_t p, const void *in, void *out, int sign, cudaStr
         cudaError_t e = cudaSuccess;
         if (!p->s_capture) e = cudaStreamCreateWithFlags(&p->s_capture, cudaStreamNonBlocking);
         if (e != cudaSuccess) return fail_cuda(e, "capture stream");
+        std::vector<PersistSeg> segs;
+        long long total = 0;
+        if (p->persist) {
+            build_segments(p, in, out, segs, total);
+            dev_free(p->d_segs);
+            int st0 = dev_alloc(p->d_segs, segs.size() * sizeof(PersistSeg), "persistent segments");
+            if (st0 != FFT_OK) return st0;
+            e = cudaMemcpy(p->d_segs.ptr, segs.data(), segs.size() * sizeof(PersistSeg), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail_cuda(e, "persistent segments upload");
+        }
         e = cudaStreamBeginCapture(p->s_capture, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
         const bool prof = p->profile;
         p->profile = false;
-        int st = exec_all(p, in, out, sign, p->s_capture);
+        int st = FFT_OK;
+        if (p->persist) {
+            cudaError_t e2 = cudaMemsetAsync(p->d_queue.ptr, 0, sizeof(unsigned long long), p->s_capture);
+            if (e2 == cudaSuccess)
+                e2 = cudaMemsetAsync(p->d_ctr.ptr, 0, sizeof(int) * (size_t)std::max(1, p->n_ctr), p->s_capture);
+            if (e2 == cudaSuccess) {
+                auto fn = p->dt == FFT_C128 ? launch_persist_f64 : launch_persist_f32;
+                e2 = fn((const PersistSeg *)p->d_segs.ptr, (int)segs.size(), total,
+                        (unsigned long long *)p->d_queue.ptr, (int *)p->d_ctr.ptr, (int *)p->err.ptr, sign,
+                        p->s_capture);
+            }
+            if (e2 != cudaSuccess) st = fail_cuda(e2, "persistent launch");
+        } else {
+            st = exec_all(p, in, out, sign, p->s_capture);
+        }
         p->profile = prof;
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(p->s_capture, &g);
@@ -1119,7 +1294,8 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
     std::string j = "{\"n\": " + std::to_string(p->n) + ", \"batch\": " + std::to_string(p->batch) +
                     ", \"dtype\": \"" + (p->dt == FFT_C128 ? "c128" : "c64") + "\", \"workspace_bytes\": " +
                     std::to_string(p->ws_bytes) + ", \"launches\": " + std::to_string(launches_per_exec(p)) +
-                    ", \"graph\": " + (p->use_graph ? "true" : "false") + ", \"form\": \"" +
+                    ", \"graph\": " + (p->use_graph ? "true" : "false") +
+                    ", \"persistent\": " + (p->persist ? "true" : "false") + ", \"form\": \"" +
                     (p->form == FFT_FORM_TC_FP16 ? "tc_fp16" : p->form == FFT_FORM_TC_BF16 ? "tc_bf16" : "plain") +
                     "\"";
     if (p->classes.size() == 1) {

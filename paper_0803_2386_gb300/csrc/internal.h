@@ -71,6 +71,27 @@ struct PassArgs {
     const void *tc_dft;
 };
 
+// One segment of a persistent launch: tickets [first, first + nctas) are the
+// tiles of the pass described by `a`.  A tile waits until counters[wait_ctr]
+// reaches wait_target (when wait_ctr >= 0) and adds one to
+// counters[signal_ctr] when done (when signal_ctr >= 0).
+struct PersistSeg {
+    PassArgs a;
+    long long first;
+    long long nctas;
+    int wait_ctr;
+    int wait_target;
+    int signal_ctr;
+    int log_r;
+    int last;
+};
+
+// persistent uneven-batch launchers (persist_f32.cu / persist_f64.cu)
+cudaError_t launch_persist_f32(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
+                               int *counters, int *err, int dir, cudaStream_t s);
+cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
+                               int *counters, int *err, int dir, cudaStream_t s);
+
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);
 cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);

@@ -63,9 +63,12 @@ inline bool tile_covers(const PassArgs &a)
     return a.A == 1 || (a.A >= W && a.A % W == 0);
 }
 
-template <typename T, int DIR, int LOGR, bool LAST>
-__global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
-    tile_kernel(PassArgs p)
+// The body of one tile, for tile index `cta` of the pass described by p,
+// with W columns (rows in the last pass) per tile and (R/16)*W threads.
+// Out-of-range tiles do no memory work but pass every barrier, so the body
+// can run inside a persistent kernel.
+template <typename T, int DIR, int LOGR, bool LAST, int W>
+__device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, typename cvec<T>::type *tile)
 {
     using V = typename cvec<T>::type;
     constexpr int R = 1 << LOGR;
@@ -73,13 +76,10 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     constexpr int L0 = LOGR - 4 * (NS - 1);  // log2 radix of the first one
     constexpr int E0 = 1 << L0;
     constexpr int U = R / 16;  // threads per column
-    constexpr int W = tile_width(LOGR);
     constexpr int G0 = 16 / E0;  // first-digit codelets per thread
     constexpr int Q0 = R / E0;
     static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *tile = reinterpret_cast<V *>(smem_raw);
     const V *twt = reinterpret_cast<const V *>(p.tw_tile);
     const V *in = reinterpret_cast<const V *>(p.in);
     V *out = reinterpret_cast<V *>(p.out);
@@ -88,7 +88,6 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     const int w = tid % W;
     const int u = tid / W;
     const int64_t n = p.n;
-    const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
 
     // ---- tile origin (load base; the store base differs only for ragged
     // batches, whose transforms sit at in_off[tr] / out_off[tr])
@@ -98,19 +97,21 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
         const int64_t colgroups = p.B / W;
         const int64_t tiles_per_tr = p.A * colgroups;
         tr = cta / tiles_per_tr;
-        if (tr >= p.count) return;
+        if (tr >= p.count) valid = false;
         const int64_t rem = cta - tr * tiles_per_tr;
         const int64_t a = rem / colgroups;
         b0 = (rem - a * colgroups) * W;
         const int64_t inner = a * (int64_t)R * p.B + b0 + w;  // element (m, this column) at base + m*B
-        base = (p.in_off ? __ldg(p.in_off + tr) : tr * n) + inner;
-        sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n) + inner;
+        if (valid) {
+            base = (p.in_off ? __ldg(p.in_off + tr) : tr * n) + inner;
+            sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n) + inner;
+        }
     } else {
         int64_t a;
         if (p.A > 1) {
             const int64_t rowgroups = p.A / W;
             tr = cta / rowgroups;
-            if (tr >= p.count) return;
+            if (tr >= p.count) valid = false;
             const int64_t q = cta - tr * rowgroups;
             vrow = q * W + w;
             // a = unrev(vrow): k^(0) is the least significant digit of vrow
@@ -126,7 +127,6 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
             }
         } else {
             const int64_t tr0 = cta * W;
-            if (tr0 >= p.count) return;
             tr = tr0 + w;
             valid = tr < p.count;
             a = 0;
@@ -250,6 +250,16 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
             out[obase + (int64_t)kk * kstride] = x;
         }
     }
+}
+
+template <typename T, int DIR, int LOGR, bool LAST>
+__global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
+    tile_kernel(PassArgs p)
+{
+    using V = typename cvec<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+    tile_body<T, DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));
 }
 
 }  // namespace moafft

@@ -37,6 +37,7 @@ def run_many(sizes, data, dt, direction=M.FFT_FORWARD, adjoint=False, reps=1):
         for _ in range(reps):
             (M.fft_exec_adjoint if adjoint else M.fft_exec)(p, d_in, d_out)
         torch.cuda.synchronize()
+        M.fft_plan_check(p)  # raises if a persistent-kernel wait timed out
         desc = M.fft_plan_describe(p)
     finally:
         M.fft_destroy(p)
@@ -91,3 +92,33 @@ def test_many_rejects_bad_sizes():
     with pytest.raises(M.MoaFFTError) as e:
         M.fft_plan_many([], M.FFT_C64)
     assert e.value.status == M.FFT_ERR_ARG
+
+
+def test_persistent_matches_per_class_graph(monkeypatch):
+    """One persistent launch (atomic ticket queue over every class and pass,
+    round counters for the pass dependencies) gives the same transforms as
+    the graph of per-class launches."""
+    sizes, data = W.uneven_batch(count=2000, seed=6)
+    y_p, desc_p = run_many(sizes, data, M.FFT_C64, reps=2)
+    monkeypatch.setenv("MOAFFT_NO_PERSIST", "1")
+    y_g, desc_g = run_many(sizes, data, M.FFT_C64)
+    assert '"persistent": true' in desc_p and '"launches": 1' in desc_p
+    assert '"persistent": false' in desc_g
+    for a, b in zip(split(y_p, sizes), split(y_g, sizes)):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dt", [M.FFT_C64, M.FFT_C128])
+def test_persistent_inverse_and_adjoint(dt):
+    sizes, data = W.uneven_batch(count=400, seed=2, lo_exp=4, hi_exp=15)
+    xr = data if dt == M.FFT_C128 else data.astype(np.complex64).astype(np.complex128)
+    tol_of = (lambda n: 1e-12) if dt == M.FFT_C128 else (lambda n: 1e-6 * np.log2(n))
+    y, desc = run_many(sizes, data, dt, M.FFT_INVERSE)
+    assert '"persistent": true' in desc
+    for yi, xi in zip(split(y, sizes), split(xr, sizes)):
+        ref = O.fft(xi[None, :], "inverse", c=64)[0]
+        assert np.linalg.norm(yi - ref) <= tol_of(len(xi)) * np.linalg.norm(ref)
+    y, _ = run_many(sizes, data, dt, M.FFT_FORWARD, adjoint=True)
+    for yi, xi in zip(split(y, sizes), split(xr, sizes)):
+        ref = O.fft(xi[None, :], "adjoint_forward", c=64)[0]
+        assert np.linalg.norm(yi - ref) <= tol_of(len(xi)) * np.linalg.norm(ref)
