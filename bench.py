@@ -516,6 +516,27 @@ def extra_configs(M, torch, dev, stream):
            "per_transform_launch_ms": round(ms_p, 3), "speedup": round(ms_p / ms_g, 1)})
     del xu, yu
 
+    # cache-blocked passes vs the unblocked routine (one HBM pass per stage)
+    for dtn, nn_, bb_, tdt in ((M.FFT_C64, 1 << 16, 4096, torch.complex64),
+                               (M.FFT_C128, 1 << 20, 64, torch.complex128)):
+        xa = torch.randn(bb_, nn_, dtype=tdt, device=dev)
+        ya = torch.empty_like(xa)
+        res = {}
+        for sched in (None, "stages"):
+            pa = M.Plan(nn_, bb_, dtn, M.FFT_FORWARD, M.FFT_FORM_PLAIN, sched)
+            res[sched or "passes"] = _time(torch, stream, lambda: pa.exec(xa, ya, stream), 3)
+            res[(sched or "passes") + "_launches"] = pa.launches
+            pa.close()
+        fl = 5.0 * nn_ * math.log2(nn_) * bb_
+        _emit({"config": f"{'c64' if dtn == M.FFT_C64 else 'c128'} n=2^{int(math.log2(nn_))} batch {bb_} "
+                         "forward: blocked passes vs one pass per stage",
+               "blocked_ms": round(res["passes"], 3), "blocked_launches": res["passes_launches"],
+               "per_stage_ms": round(res["stages"], 3), "per_stage_launches": res["stages_launches"],
+               "blocked_gflops": round(fl / (res["passes"] * 1e-3) / 1e9, 1),
+               "per_stage_gflops": round(fl / (res["stages"] * 1e-3) / 1e9, 1),
+               "speedup": round(res["stages"] / res["passes"], 2)})
+        del xa, ya
+
     # differentiation: complex64 n = 2^18, batch 256, forward + adjoint
     n, batch = 1 << 18, 256
     xd = torch.randn(batch, n, dtype=torch.complex64, device=dev)

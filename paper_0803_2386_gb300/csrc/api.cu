@@ -239,11 +239,22 @@ static int build_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
         if (chunk) *chunk = k;
     }
     if (body.empty() || body == "auto") return default_schedule(s, n, dt);
+    if (body == "stages") {
+        s = Schedule();
+        s.n = n;
+        s.t = exact_log2(n);
+        s.unblocked = true;
+        s.npass = 0;
+        return FFT_OK;
+    }
     return parse_schedule(s, n, dt, body.c_str());
 }
 
 static std::string schedule_json(const Schedule &s)
 {
+    if (s.unblocked)
+        return "{\"n\": " + std::to_string(s.n) + ", \"unblocked\": true, \"stages\": " + std::to_string(s.t) +
+               ", \"passes\": []}";
     std::string j = "{\"n\": " + std::to_string(s.n) + ", \"passes\": [";
     for (int i = 0; i < s.npass; i++) {
         const PassDesc &p = s.pass[i];
@@ -458,6 +469,7 @@ size_t pass_smem_bytes(const PassArgs &a, size_t eb)
 
 static int64_t class_launches(const SizeClass &c)
 {
+    if (c.sched.unblocked) return 1 + c.sched.t;
     if (c.sched.npass == 1) return 1;
     return (c.count + c.chunk - 1) / c.chunk * c.sched.npass;
 }
@@ -477,6 +489,10 @@ static int make_tables(fft_plan_s *p)
     size_t eb = elem_bytes(p->dt);
     size_t off = 0;
     for (auto &c : p->classes) {
+        if (c.sched.unblocked) {
+            c.sched.pass[0].tw_pass_off = off;
+            off += (size_t)std::max<int64_t>(1, c.n / 2);
+        }
         for (int i = 0; i < c.sched.npass; i++) {
             PassDesc &d = c.sched.pass[i];
             d.tw_tile_off = off;
@@ -495,6 +511,14 @@ static int make_tables(fft_plan_s *p)
     int st = dev_alloc(p->tw, off * eb, "twiddle tables");
     if (st != FFT_OK) return st;
     for (auto &c : p->classes) {
+        if (c.sched.unblocked && c.n > 1) {
+            cudaError_t e = p->dt == FFT_C128
+                                ? launch_twiddle_f64((double *)p->tw.ptr + 2 * c.sched.pass[0].tw_pass_off, c.n / 2,
+                                                     c.n, 1, 0)
+                                : launch_twiddle_f32((float *)p->tw.ptr + 2 * c.sched.pass[0].tw_pass_off, c.n / 2,
+                                                     c.n, 1, 0);
+            if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
+        }
         for (int i = 0; i < c.sched.npass; i++) {
             PassDesc &d = c.sched.pass[i];
             int64_t R = (int64_t)1 << d.log_r;
@@ -574,7 +598,10 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
     const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)32 << 20);
     int64_t ws = 0;
     for (auto &c : p->classes) {
-        if (c.sched.npass > 1) {
+        if (c.sched.unblocked) {
+            c.chunk = c.count;
+            ws = std::max<int64_t>(ws, c.count * c.n * (int64_t)eb);  // for in-place calls
+        } else if (c.sched.npass > 1) {
             c.chunk = std::max<int64_t>(1, std::min<int64_t>(c.count, target / (c.n * (int64_t)eb)));
             if (req_chunk > 0) c.chunk = std::min<int64_t>(c.count, req_chunk);
             ws = std::max<int64_t>(ws, c.chunk * c.n * (int64_t)eb);
@@ -889,6 +916,15 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
     const Schedule &S = C.sched;
     const double scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)C.n : 1.0;
     const bool ragged = C.d_off.ptr != nullptr;
+    if (S.unblocked) {
+        if (ragged) return fail(FFT_ERR_UNSUPPORTED, "the per-stage schedule takes dense batches");
+        const char *src = (const char *)in + (size_t)t0 * C.n * eb;
+        char *dst = (char *)out + (size_t)t0 * C.n * eb;
+        cudaError_t e = launch_stages(p->dt == FFT_C128, src, dst, p->ws.ptr, C.n, cnt,
+                                      (const char *)p->tw.ptr + S.pass[0].tw_pass_off * eb, sign, scale, s);
+        if (e != cudaSuccess) return fail_cuda(e, "per-stage launch");
+        return FFT_OK;
+    }
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.n = C.n;

@@ -39,6 +39,10 @@ struct Schedule {
     int t = 0;
     int npass = 0;
     PassDesc pass[kMaxPasses];
+    // schedule "stages": the unblocked routine, one HBM pass per radix-2
+    // stage after a bit-reversal pass (stages.cu); pass[0].tw_pass_off then
+    // locates the table w_n^e, e < n/2
+    bool unblocked = false;
 };
 
 // Parameters of one pass launch (passed by value to the kernel).
@@ -91,6 +95,11 @@ cudaError_t launch_persist_f32(const PersistSeg *segs, int nseg, long long total
                                int *counters, int *err, int dir, cudaStream_t s);
 cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
                                int *counters, int *err, int dir, cudaStream_t s);
+
+// unblocked per-stage transform (stages.cu); tmp (n * count elements) is
+// used when in == out
+cudaError_t launch_stages(bool f64, const void *in, void *out, void *tmp, int64_t n, int64_t count, const void *tw,
+                          int dir, double scale, cudaStream_t s);
 
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);

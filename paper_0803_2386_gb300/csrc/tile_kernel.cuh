@@ -63,12 +63,17 @@ inline bool tile_covers(const PassArgs &a)
     return a.A == 1 || (a.A >= W && a.A % W == 0);
 }
 
-// The body of one tile, for tile index `cta` of the pass described by p,
-// with W columns (rows in the last pass) per tile and (R/16)*W threads.
-// Out-of-range tiles do no memory work but pass every barrier, so the body
-// can run inside a persistent kernel.
-template <typename T, int DIR, int LOGR, bool LAST, int W>
-__device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, typename cvec<T>::type *tile)
+// Where tile `cta` of the pass described by p starts (load and store bases,
+// first column, transform, row of the final transpose).  Out-of-range tiles
+// come back with valid = false: they do no memory work but pass every
+// barrier, so the tile can run inside a persistent kernel.
+struct TileRef {
+    int64_t base = 0, sbase = 0, b0 = 0, tr = 0, vrow = 0;
+    bool valid = true;
+};
+
+template <typename T, int LOGR, bool LAST, int W>
+__device__ __forceinline__ TileRef tile_ref(const PassArgs &p, const int64_t cta)
 {
     using V = typename cvec<T>::type;
     constexpr int R = 1 << LOGR;
@@ -79,20 +84,16 @@ __device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, 
     constexpr int G0 = 16 / E0;  // first-digit codelets per thread
     constexpr int Q0 = R / E0;
     static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
-
-    const V *twt = reinterpret_cast<const V *>(p.tw_tile);
-    const V *in = reinterpret_cast<const V *>(p.in);
-    V *out = reinterpret_cast<V *>(p.out);
-
     const int tid = threadIdx.x;
     const int w = tid % W;
     const int u = tid / W;
     const int64_t n = p.n;
-
+    (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
     // ---- tile origin (load base; the store base differs only for ragged
     // batches, whose transforms sit at in_off[tr] / out_off[tr])
-    int64_t base = 0, sbase = 0, b0 = 0, tr = 0, vrow = 0;
-    bool valid = true;
+    TileRef r;
+    int64_t &base = r.base, &sbase = r.sbase, &b0 = r.b0, &tr = r.tr, &vrow = r.vrow;
+    bool &valid = r.valid;
     if constexpr (!LAST) {
         const int64_t colgroups = p.B / W;
         const int64_t tiles_per_tr = p.A * colgroups;
@@ -137,9 +138,31 @@ __device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, 
             sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n);
         }
     }
-    const int64_t mstride = LAST ? 1 : p.B;
+    return r;
+}
 
-    V v[16];
+// 1. HBM -> registers: the thread's points of its first-digit codelets
+template <typename T, int LOGR, bool LAST, int W>
+__device__ __forceinline__ void tile_load(const PassArgs &p, const TileRef &r, typename cvec<T>::type *v)
+{
+    using V = typename cvec<T>::type;
+    constexpr int R = 1 << LOGR;
+    constexpr int NS = (LOGR + 3) / 4;       // sub-passes
+    constexpr int L0 = LOGR - 4 * (NS - 1);  // log2 radix of the first one
+    constexpr int E0 = 1 << L0;
+    constexpr int U = R / 16;  // threads per column
+    constexpr int G0 = 16 / E0;  // first-digit codelets per thread
+    constexpr int Q0 = R / E0;
+    static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
+    const int tid = threadIdx.x;
+    const int w = tid % W;
+    const int u = tid / W;
+    const int64_t n = p.n;
+    (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
+    const V *in = reinterpret_cast<const V *>(p.in);
+    const int64_t mstride = LAST ? 1 : p.B;
+    const int64_t base = r.base;
+    const bool valid = r.valid;
     // ---- 1. HBM -> registers, first digit (radix E0)
 #pragma unroll
     for (int g = 0; g < G0; g++)
@@ -150,6 +173,32 @@ __device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, 
             else { v[g * E0 + e].x = 0; v[g * E0 + e].y = 0; }
         }
 
+}
+
+// 2.-4. codelets, shared-memory exchanges, weights, stores
+template <typename T, int DIR, int LOGR, bool LAST, int W>
+__device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r, typename cvec<T>::type *v,
+                                            typename cvec<T>::type *tile)
+{
+    using V = typename cvec<T>::type;
+    constexpr int R = 1 << LOGR;
+    constexpr int NS = (LOGR + 3) / 4;       // sub-passes
+    constexpr int L0 = LOGR - 4 * (NS - 1);  // log2 radix of the first one
+    constexpr int E0 = 1 << L0;
+    constexpr int U = R / 16;  // threads per column
+    constexpr int G0 = 16 / E0;  // first-digit codelets per thread
+    constexpr int Q0 = R / E0;
+    static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
+    const int tid = threadIdx.x;
+    const int w = tid % W;
+    const int u = tid / W;
+    const int64_t n = p.n;
+    (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
+    const V *twt = reinterpret_cast<const V *>(p.tw_tile);
+    V *out = reinterpret_cast<V *>(p.out);
+    const int64_t sbase = r.sbase, b0 = r.b0, tr = r.tr, vrow = r.vrow;
+    const bool valid = r.valid;
+    (void)tr;
     // ---- 2. first-digit codelets
 #pragma unroll
     for (int g = 0; g < G0; g++) {
@@ -250,6 +299,18 @@ __device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, 
             out[obase + (int64_t)kk * kstride] = x;
         }
     }
+}
+
+
+// The body of one tile, for tile index `cta` of the pass described by p,
+// with W columns (rows in the last pass) per tile and (R/16)*W threads.
+template <typename T, int DIR, int LOGR, bool LAST, int W>
+__device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, typename cvec<T>::type *tile)
+{
+    typename cvec<T>::type v[16];
+    const TileRef r = tile_ref<T, LOGR, LAST, W>(p, cta);
+    tile_load<T, LOGR, LAST, W>(p, r, v);
+    tile_finish<T, DIR, LOGR, LAST, W>(p, r, v, tile);
 }
 
 template <typename T, int DIR, int LOGR, bool LAST>

@@ -130,3 +130,8 @@ def test_tune_candidates_are_valid_schedules(t, dt):
     for c in cands:
         s = json.loads(M.fft_describe_schedule(1 << t, dt, M.FFT_FORM_PLAIN, c))
         assert sum(p["log_r"] for p in s["passes"]) == t
+
+
+def test_unblocked_schedule_describes_stages():
+    s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "stages"))
+    assert s["unblocked"] and s["stages"] == 12 and s["passes"] == []

@@ -222,3 +222,22 @@ def test_full_size_c64_sampled():
     y = d_out[picks].cpu().numpy().astype(np.complex128)
     ref = O.fft(rounded(x[picks], M.FFT_C64), "forward", c=1024, threads=3)
     assert rel_rows(y, ref).max() <= 1e-6 * 16
+
+
+# ------------------------------------- unblocked routine (one pass per stage)
+
+@pytest.mark.parametrize("dt", [M.FFT_C128, M.FFT_C64])
+@pytest.mark.parametrize("t", [0, 1, 2, 5, 10, 13])
+def test_unblocked_stages(dt, t):
+    """Schedule "stages": bit reversal, then one HBM pass per radix-2 stage
+    with the hyper-cube ONF pairs (the paper's fftpsirad2 on the GPU)."""
+    n = 1 << t
+    x = W.uniform_complex(n, 3, seed=200 + t)
+    xr = rounded(x, dt)
+    for direction in (M.FFT_FORWARD, M.FFT_INVERSE):
+        y = run_plan(x, dt, direction, schedule="stages")
+        assert rel_rows(y, oracle_op(xr, direction, False)).max() <= tol(dt, n)
+    y = run_plan(x, dt, M.FFT_FORWARD, adjoint=True, schedule="stages")
+    assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, True)).max() <= tol(dt, n)
+    y = run_plan(x, dt, M.FFT_FORWARD, schedule="stages", inplace=True)
+    assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, False)).max() <= tol(dt, n)
