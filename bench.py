@@ -485,14 +485,14 @@ def extra_configs(M, torch, dev, stream):
     sizes, data = W.uneven_batch()
     xu = torch.from_numpy(data).to(torch.complex64).to(dev)
     yu = torch.empty_like(xu)
+    os.environ["MOAFFT_PERSIST"] = "1"
     pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
+    del os.environ["MOAFFT_PERSIST"]
     ms_pers = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
     M.fft_plan_check(pm)
     pers = json.loads(M.fft_plan_describe(pm))["persistent"]
     M.fft_destroy(pm)
-    os.environ["MOAFFT_NO_PERSIST"] = "1"
     pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
-    del os.environ["MOAFFT_NO_PERSIST"]
     ms_g = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
     launches = M.fft_plan_launches(pm)
     M.fft_destroy(pm)

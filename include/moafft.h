@@ -93,9 +93,15 @@ int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir
 
 /* Uneven batch: `count` transforms of power-of-two lengths sizes[i] (host
  * array, copied), packed back to back in the order given (transform i starts
- * at element sum_{j<i} sizes[j]).  Executed as one persistent, graph-captured
- * launch sequence.  Cite: Ch.3 "The Number of Reshape-Transpose Operations"
- * (the schedule is chosen per length). */
+ * at element sum_{j<i} sizes[j]).  The transforms are grouped by length
+ * (each length gets its own pass schedule, from the autotuner cache when
+ * present) and every execution replays one captured CUDA graph.  By default
+ * the graph holds the per-length pass launches; with the environment
+ * variable MOAFFT_PERSIST=1 at plan time it holds a single persistent kernel
+ * whose CTAs take tiles of every length and pass from one atomic ticket
+ * queue, the second pass of each workspace round waiting (bounded) on
+ * counters the first pass signals.  Cite: Ch.3 "The Number of
+ * Reshape-Transpose Operations" (the schedule is chosen per length). */
 int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t count, fft_dtype dt,
                   fft_dir dir);
 

@@ -592,10 +592,10 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
         return fail_cuda(e, "cudaGetDevice");
     }
     size_t eb = elem_bytes(p->dt);
-    // complex64 passes are HBM-bound, so a workspace round stays L2-resident
-    // (32 MiB); complex128 passes are FP64-bound, so larger rounds (256 MiB)
-    // cut the launch count and the wave tails
-    const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)32 << 20);
+    // transforms per workspace round: 256 MiB of complex128 (FP64-bound
+    // passes: fewer launches and wave tails), 512 MiB of complex64 (measured:
+    // L2-sized rounds cost more in launch tails than their L2 reuse saves)
+    const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)512 << 20);
     int64_t ws = 0;
     for (auto &c : p->classes) {
         if (c.sched.unblocked) {
@@ -870,7 +870,10 @@ extern "C" int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t coun
         if (st != FFT_OK) break;
     }
     if (st == FFT_OK) st = finish_plan(p, 0);
-    if (st == FFT_OK && !getenv("MOAFFT_NO_PERSIST")) st = try_persist(p);
+    // one persistent launch (MOAFFT_PERSIST=1) or, by default, the graph of
+    // per-class launches, which is faster since its row tiles are TMA-staged
+    const char *pers = getenv("MOAFFT_PERSIST");
+    if (st == FFT_OK && pers && *pers == '1') st = try_persist(p);
     if (st != FFT_OK) {
         destroy_plan(p);
         return st;

@@ -142,3 +142,28 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k)
 
 }  // namespace tc
 }  // namespace moafft
+
+namespace moafft {
+namespace tc {
+
+// ---- bulk async copies (the TMA engine, untiled form) -------------------
+// arrive on the mbarrier and raise its expected transaction count by bytes
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned); completion is reported to the mbarrier as transaction bytes
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+}  // namespace tc
+}  // namespace moafft

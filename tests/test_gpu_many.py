@@ -99,8 +99,9 @@ def test_persistent_matches_per_class_graph(monkeypatch):
     round counters for the pass dependencies) gives the same transforms as
     the graph of per-class launches."""
     sizes, data = W.uneven_batch(count=2000, seed=6)
+    monkeypatch.setenv("MOAFFT_PERSIST", "1")
     y_p, desc_p = run_many(sizes, data, M.FFT_C64, reps=2)
-    monkeypatch.setenv("MOAFFT_NO_PERSIST", "1")
+    monkeypatch.delenv("MOAFFT_PERSIST")
     y_g, desc_g = run_many(sizes, data, M.FFT_C64)
     assert '"persistent": true' in desc_p and '"launches": 1' in desc_p
     assert '"persistent": false' in desc_g
@@ -109,7 +110,8 @@ def test_persistent_matches_per_class_graph(monkeypatch):
 
 
 @pytest.mark.parametrize("dt", [M.FFT_C64, M.FFT_C128])
-def test_persistent_inverse_and_adjoint(dt):
+def test_persistent_inverse_and_adjoint(dt, monkeypatch):
+    monkeypatch.setenv("MOAFFT_PERSIST", "1")
     sizes, data = W.uneven_batch(count=400, seed=2, lo_exp=4, hi_exp=15)
     xr = data if dt == M.FFT_C128 else data.astype(np.complex64).astype(np.complex128)
     tol_of = (lambda n: 1e-12) if dt == M.FFT_C128 else (lambda n: 1e-6 * np.log2(n))
