@@ -9,12 +9,15 @@
 // tiles ahead.  While tile i is being computed and stored, the copies of
 // tiles i+1 and i+2 are in flight, without holding any registers.
 //
-//   non-last pass: the tile's R rows of W contiguous columns (W*8 bytes each,
-//     at stride B) land as an R x W block;
-//   last pass: its W rows of R contiguous points land as W padded rows.
+//   non-last pass (column tiles): the signal is a 2-D tensor of rows of B
+//     points; a tensor map describes it and the tile's R x W box arrives in
+//     boxes of at most 256 rows through cp.async.bulk.tensor.2d;
+//   last pass (row tiles): its W rows of R contiguous points arrive as one
+//     bulk copy per row, into padded rows.
 // Every wait is bounded; a timeout is recorded in the error word.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,7 +46,8 @@ __host__ __device__ constexpr size_t bulk_smem_bytes()
 
 // warp 0: start the copies of tile `cta` into stage `buf`
 template <int LOGR, bool LAST>
-__device__ __forceinline__ void bulk_issue(const PassArgs &p, long long cta, float2 *stage, uint64_t *mbar)
+__device__ __forceinline__ void bulk_issue(const PassArgs &p, const CUtensorMap *tmap, long long cta, float2 *stage,
+                                           uint64_t *mbar)
 {
     constexpr int R = 1 << LOGR;
     constexpr int W = tile_width(LOGR);
@@ -57,11 +61,15 @@ __device__ __forceinline__ void bulk_issue(const PassArgs &p, long long cta, flo
         const int64_t rem = cta - tr * tiles_per_tr;
         const int64_t a = rem / colgroups;
         const int64_t b0 = (rem - a * colgroups) * W;
-        const int64_t base = tr * n + a * (int64_t)R * p.B + b0;
-        if (lane == 0) tc::mbar_arrive_expect_tx(mbar, (uint32_t)(R * W * sizeof(float2)));
-        __syncwarp();
-        for (int m = lane; m < R; m += 32)
-            tc::bulk_g2s(stage + (size_t)m * W, in + base + (int64_t)m * p.B, W * sizeof(float2), mbar);
+        // rows of the 2-D view: (tr * A + a) * R + m, columns b
+        constexpr int BR = R < 256 ? R : 256;
+        if (lane == 0) {
+            tc::mbar_arrive_expect_tx(mbar, (uint32_t)(R * W * sizeof(float2)));
+            const int y0 = (int)((tr * p.A + a) * R);
+            for (int k = 0; k < R / BR; k++)
+                tc::tensor_g2s_2d(stage + (size_t)k * BR * W, tmap, (int)b0, y0 + k * BR, mbar);
+        }
+        (void)in;
     } else {
         int64_t tr0;
         int rows;
@@ -99,7 +107,8 @@ __device__ __forceinline__ void bulk_issue(const PassArgs &p, long long cta, flo
 }
 
 template <int DIR, int LOGR, bool LAST>
-__global__ void __launch_bounds__(tile_threads(LOGR), 2) bulk_kernel(PassArgs p, long long total)
+__global__ void __launch_bounds__(tile_threads(LOGR), 2)
+    bulk_kernel(PassArgs p, long long total, const __grid_constant__ CUtensorMap tmap)
 {
     using V = float2;
     constexpr int R = 1 << LOGR;
@@ -126,8 +135,8 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) bulk_kernel(PassArgs p,
     }
     __syncthreads();
     if (tid < 32) {
-        bulk_issue<LOGR, LAST>(p, t, stage, &mbar[0]);
-        if (t + G < total) bulk_issue<LOGR, LAST>(p, t + G, stage + SE, &mbar[1]);
+        bulk_issue<LOGR, LAST>(p, &tmap, t, stage, &mbar[0]);
+        if (t + G < total) bulk_issue<LOGR, LAST>(p, &tmap, t + G, stage + SE, &mbar[1]);
     }
     for (int it = 0; t < total; t += G, it++) {
         const int buf = it & 1;
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) bulk_kernel(PassArgs p,
         __syncthreads();  // every thread has read this stage
         if (tid < 32 && t + 2 * G < total) {
             tc::fence_proxy_async();
-            bulk_issue<LOGR, LAST>(p, t + 2 * G, stage + buf * SE, &mbar[buf]);
+            bulk_issue<LOGR, LAST>(p, &tmap, t + 2 * G, stage + buf * SE, &mbar[buf]);
         }
         tile_finish<float, DIR, LOGR, LAST, W>(p, r, v, tile);
         __syncthreads();  // the next tile reuses the exchange tile

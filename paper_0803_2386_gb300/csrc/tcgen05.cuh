@@ -165,5 +165,18 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, u
         : "memory");
 }
 
+// 2-D tiled tensor copy global -> shared through a tensor map (the TMA
+// unit proper): the box at coordinates (x, y) of the map lands row-major at
+// smem_dst; completion is counted in bytes on the mbarrier.  x * element
+// size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_g2s_2d(void *smem_dst, const void *tmap, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(smem_dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace moafft

@@ -3,6 +3,7 @@
 #include "bulk_kernel.cuh"
 
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -37,6 +38,45 @@ static cudaError_t launch_tile_one(const PassArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled, reached through the runtime (no link to libcuda)
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// The tensor map of a column pass: rows of B points (8 bytes each), one row
+// per (transform, a, m); boxes of W columns by min(R, 256) rows.
+static bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const int R = 1 << a.log_r;
+    cuuint64_t dims[2] = {(cuuint64_t)a.B, (cuuint64_t)(a.count * a.A * R)};
+    cuuint64_t strides[1] = {(cuuint64_t)a.B * 8};
+    cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)(R < 256 ? R : 256)};
+    cuuint32_t estr[2] = {1, 1};
+    if (dims[1] > 0xffffffffULL) return false;
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(a.in), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // persistent form with TMA-staged loads (bulk_kernel.cuh)
 template <int DIR, int LOGR, bool LAST>
 static cudaError_t launch_bulk_one(const PassArgs &a, cudaStream_t s)
@@ -65,7 +105,10 @@ static cudaError_t launch_bulk_one(const PassArgs &a, cudaStream_t s)
     else ctas = (a.count + W - 1) / W;
     if (ctas <= 0) return cudaSuccess;
     const int64_t grid = std::min<int64_t>(ctas, (int64_t)sms * per_sm);
-    bulk_kernel<DIR, LOGR, LAST><<<(unsigned)grid, tile_threads(LOGR), smem, s>>>(a, (long long)ctas);
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    if (!LAST && !column_tensor_map(a, W, &map)) return cudaErrorNotSupported;
+    bulk_kernel<DIR, LOGR, LAST><<<(unsigned)grid, tile_threads(LOGR), smem, s>>>(a, (long long)ctas, map);
     return cudaGetLastError();
 }
 
@@ -102,13 +145,15 @@ static cudaError_t launch_tile_dir(const PassArgs &a, cudaStream_t s)
 
 cudaError_t launch_tile_f32(const PassArgs &a, int dir, cudaStream_t s)
 {
-    // TMA-staged form for row tiles (the last pass: W rows of R contiguous
-    // points, one bulk copy per row); column tiles keep plain loads, whose
-    // rows of W points are too short for the copy engine to pay off
+    // TMA-staged form: row tiles (the last pass) by one bulk copy per row,
+    // column tiles by 2-D tensor-map boxes; dense, 16-byte aligned input
     static const bool bulk = getenv("MOAFFT_NO_BULK") == nullptr;
-    if (bulk && a.is_last && bulk_ok(a.log_r) && a.in_off == nullptr && ((uintptr_t)a.in % 16) == 0) {
-        if (dir < 0) return a.is_last ? launch_bulk_dir<-1, true>(a, s) : launch_bulk_dir<-1, false>(a, s);
-        return a.is_last ? launch_bulk_dir<1, true>(a, s) : launch_bulk_dir<1, false>(a, s);
+    static const bool cols = getenv("MOAFFT_NO_TMA_COLUMNS") == nullptr;
+    if (bulk && (a.is_last || cols) && bulk_ok(a.log_r) && a.in_off == nullptr && ((uintptr_t)a.in % 16) == 0) {
+        cudaError_t e;
+        if (dir < 0) e = a.is_last ? launch_bulk_dir<-1, true>(a, s) : launch_bulk_dir<-1, false>(a, s);
+        else e = a.is_last ? launch_bulk_dir<1, true>(a, s) : launch_bulk_dir<1, false>(a, s);
+        if (e != cudaErrorNotSupported) return e;
     }
     if (dir < 0) return a.is_last ? launch_tile_dir<-1, true>(a, s) : launch_tile_dir<-1, false>(a, s);
     return a.is_last ? launch_tile_dir<1, true>(a, s) : launch_tile_dir<1, false>(a, s);
