@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c64", "tc_fp16", "tc_bf16"],
-                    help="small profiling case: complex64 n=2^16 batch 512 forward, three runs")
+    ap.add_argument("--case", default="", choices=["", "c64", "tc_fp16", "tc_bf16", "c128", "df64"],
+                    help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
+                         "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
                     help="also measure the other configurations (latency, precision forms, uneven "
                          "batch, forward+adjoint); one JSON line each on stderr")
@@ -516,6 +517,36 @@ def extra_configs(M, torch, dev, stream):
            "per_transform_launch_ms": round(ms_p, 3), "speedup": round(ms_p / ms_g, 1)})
     del xu, yu
 
+    # complex128 at FP64 accuracy: native FP64 vs double-float butterflies
+    n, batch = 1 << 20, 64
+    xd = torch.rand(batch, n, dtype=torch.complex128, device=dev) * 2 - (1 + 1j)
+    yd = torch.empty_like(xd)
+    rd = torch.empty_like(xd)
+    res = {}
+    for form, name in ((M.FFT_FORM_PLAIN, "fp64"), (M.FFT_FORM_DF64, "df64")):
+        pf = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD, form)
+        pi = M.Plan(n, batch, M.FFT_C128, M.FFT_INVERSE, form)
+
+        def fwd_inv():
+            pf.exec(xd, yd, stream)
+            pi.exec(yd, rd, stream)
+
+        res[name] = _time(torch, stream, fwd_inv, 5)
+        if name == "fp64":
+            ref = yd.clone()
+        else:
+            res["df64_err"] = rel(yd, ref)
+        res[name + "_rt"] = rel(rd, xd)
+        pf.close()
+        pi.close()
+    fl = 2 * 5.0 * n * 20 * batch
+    _emit({"config": "c128 n=2^20 batch 64 forward+inverse: FP64 vs double-float",
+           "fp64_ms": round(res["fp64"], 3), "fp64_gflops": round(fl / (res["fp64"] * 1e-3) / 1e9, 1),
+           "df64_ms": round(res["df64"], 3), "df64_gflops": round(fl / (res["df64"] * 1e-3) / 1e9, 1),
+           "df64_rel_err_vs_fp64": res["df64_err"], "df64_roundtrip_err": res["df64_rt"],
+           "speedup": round(res["fp64"] / res["df64"], 2)})
+    del xd, yd, rd, ref
+
     # cache-blocked passes vs the unblocked routine (one HBM pass per stage)
     for dtn, nn_, bb_, tdt in ((M.FFT_C64, 1 << 16, 4096, torch.complex64),
                                (M.FFT_C128, 1 << 20, 64, torch.complex128)):
@@ -569,11 +600,18 @@ def run_case(args):
     """A small case for ncu captures of the complex64 kernels."""
     import torch
     import paper_0803_2386_gb300 as M
-    form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16}[args.case]
-    n, batch = 1 << 16, 512
-    x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
-    y = torch.empty_like(x)
-    p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form, "8,8;chunk=512")
+    form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
+            "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64}[args.case]
+    if args.case in ("c128", "df64"):
+        n, batch = 1 << 20, 16
+        x = torch.randn(batch, n, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD, form)
+    else:
+        n, batch = 1 << 16, 512
+        x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form, "8,8;chunk=512")
     for _ in range(3):
         p.exec(x, y)
     M.fft_plan_check(p.handle)

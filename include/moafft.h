@@ -53,11 +53,18 @@ typedef enum { FFT_FORWARD = -1, FFT_INVERSE = 1 } fft_dir;
  * FFT_FORM_TC_FP16 / FFT_FORM_TC_BF16 (C64 only): radix-16 DFT stages as
  *   tensor-core matrix products with split (hi + lo) FP16 or BF16 operands
  *   and FP32 accumulation (the radix-n DFT of the general-radix routine,
- *   Fig. radnbutterfly, written as a dense product). */
+ *   Fig. radnbutterfly, written as a dense product).
+ * FFT_FORM_DF64 (C128 only, n >= 16): the same butterflies in double-float
+ *   arithmetic -- each double carried as an unevaluated sum of two floats
+ *   (about 48 significant bits) computed on the FP32 pipes, with complex128
+ *   kept as the memory format; relative error of a few 1e-15 per operation.
+ *   Needs every pass to be a tile of 2^4..2^12 points (the default
+ *   schedules are); FFT_ERR_UNSUPPORTED otherwise. */
 typedef enum {
     FFT_FORM_PLAIN = 0,
     FFT_FORM_TC_FP16 = 1,
-    FFT_FORM_TC_BF16 = 2
+    FFT_FORM_TC_BF16 = 2,
+    FFT_FORM_DF64 = 3
 } fft_form;
 
 typedef enum {

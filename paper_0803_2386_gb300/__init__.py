@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(PKG_DIR, "libmoafft.so")
 
 FFT_C64, FFT_C128 = 0, 1
 FFT_FORWARD, FFT_INVERSE = -1, 1
-FFT_FORM_PLAIN, FFT_FORM_TC_FP16, FFT_FORM_TC_BF16 = 0, 1, 2
+FFT_FORM_PLAIN, FFT_FORM_TC_FP16, FFT_FORM_TC_BF16, FFT_FORM_DF64 = 0, 1, 2, 3
 
 FFT_OK = 0
 FFT_ERR_ARG = -1

@@ -523,6 +523,8 @@ static int make_tables(fft_plan_s *p)
             PassDesc &d = c.sched.pass[i];
             int64_t R = (int64_t)1 << d.log_r;
             auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
+                if (p->form == FFT_FORM_DF64)
+                    return launch_twiddle_df64((float *)p->tw.ptr + 4 * o, count, m, stride, 0);
                 if (p->dt == FFT_C128)
                     return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
                 return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
@@ -644,10 +646,12 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     int st = check_common(n, dt, dir);
     if (st != FFT_OK) return st;
     if (batch < 1) return fail(FFT_ERR_ARG, "batch = %lld < 1", (long long)batch);
-    if (form != FFT_FORM_PLAIN && form != FFT_FORM_TC_FP16 && form != FFT_FORM_TC_BF16)
+    if (form != FFT_FORM_PLAIN && form != FFT_FORM_TC_FP16 && form != FFT_FORM_TC_BF16 && form != FFT_FORM_DF64)
         return fail(FFT_ERR_ARG, "unknown form %d", (int)form);
-    if (form != FFT_FORM_PLAIN && dt != FFT_C64)
+    if ((form == FFT_FORM_TC_FP16 || form == FFT_FORM_TC_BF16) && dt != FFT_C64)
         return fail(FFT_ERR_UNSUPPORTED, "the tensor-core forms take complex64 data");
+    if (form == FFT_FORM_DF64 && dt != FFT_C128)
+        return fail(FFT_ERR_UNSUPPORTED, "the double-float form takes complex128 data");
     std::string chosen = schedule ? schedule : "";
     if (chosen == "auto") {
         int st2 = autotune(n, batch, dt, dir, form, chosen);
@@ -670,6 +674,17 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     c.count = batch;
     int64_t req_chunk = 0;
     st = build_schedule(c.sched, n, dt, schedule, &req_chunk);
+    if (st == FFT_OK && form == FFT_FORM_DF64) {
+        bool ok = !c.sched.unblocked && c.sched.npass > 0;
+        for (int i = 0; ok && i < c.sched.npass; i++) {
+            const PassDesc &d = c.sched.pass[i];
+            const int64_t W = std::min(32, std::max(1, 4096 >> d.log_r));
+            const bool last = i == c.sched.npass - 1;
+            ok = d.log_r >= 4 && d.log_r <= 12 && d.width == W &&
+                 (last ? (d.A == 1 || (d.A >= W && d.A % W == 0)) : (d.B >= W && d.B % W == 0));
+        }
+        if (!ok) st = fail(FFT_ERR_UNSUPPORTED, "the double-float form needs passes of 2^4..2^12 points (n >= 16)");
+    }
     if (st == FFT_OK) st = finish_plan(p, req_chunk);
     if (st != FFT_OK) {
         destroy_plan(p);
@@ -967,7 +982,8 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
                 if (rec.a) cudaEventRecord(rec.a, s);
             }
             cudaError_t e;
-            if (p->dt == FFT_C128) e = launch_pass_f64(a, sign, s);
+            if (p->form == FFT_FORM_DF64) e = launch_tile_df64(a, sign, s);
+            else if (p->dt == FFT_C128) e = launch_pass_f64(a, sign, s);
             else if (p->form != FFT_FORM_PLAIN && tc_covers(a))
                 e = launch_tc_f32(a, sign, p->form == FFT_FORM_TC_BF16, s);
             else e = launch_pass_f32(a, sign, s);
@@ -1335,7 +1351,10 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
                     std::to_string(p->ws_bytes) + ", \"launches\": " + std::to_string(launches_per_exec(p)) +
                     ", \"graph\": " + (p->use_graph ? "true" : "false") +
                     ", \"persistent\": " + (p->persist ? "true" : "false") + ", \"form\": \"" +
-                    (p->form == FFT_FORM_TC_FP16 ? "tc_fp16" : p->form == FFT_FORM_TC_BF16 ? "tc_bf16" : "plain") +
+                    (p->form == FFT_FORM_TC_FP16   ? "tc_fp16"
+                     : p->form == FFT_FORM_TC_BF16 ? "tc_bf16"
+                     : p->form == FFT_FORM_DF64    ? "df64"
+                                                   : "plain") +
                     "\"";
     if (p->classes.size() == 1) {
         j += ", \"chunk\": " + std::to_string(p->classes[0].chunk) + ", \"schedule\": " +

@@ -64,34 +64,45 @@ __host__ __device__ __forceinline__ V c_rot(V a)
     return r;
 }
 
+// x in direction DIR: -x when DIR < 0 (multiplication by s = DIR without a
+// product, so the same code serves scalar types whose products are costly)
+template <int DIR, typename T>
+__host__ __device__ __forceinline__ T sgn(T x)
+{
+    if constexpr (DIR < 0) return -x;
+    else return x;
+}
+
 // multiply by w_16^J in direction DIR, J in {0..9}; constants are
-// cos/sin of multiples of pi/8.
+// cos/sin of multiples of pi/8 (held as doubles, converted to the scalar type)
 template <int DIR, int J, typename V>
 __host__ __device__ __forceinline__ V c_w16(V a)
 {
     using T = decltype(a.x);
-    constexpr T C1 = (T)0.92387953251128675613;  // cos(pi/8)
-    constexpr T S1 = (T)0.38268343236508977173;  // sin(pi/8)
-    constexpr T H = (T)0.70710678118654752440;   // sqrt(2)/2
-    constexpr T s = (T)DIR;
+    constexpr double C1 = 0.92387953251128675613;  // cos(pi/8)
+    constexpr double S1 = 0.38268343236508977173;  // sin(pi/8)
+    constexpr double H = 0.70710678118654752440;   // sqrt(2)/2
     if constexpr (J == 0) {
         return a;
     } else if constexpr (J == 4) {
         return c_rot<DIR>(a);
     } else if constexpr (J == 2) {  // H*(1 + s i)
+        constexpr T h = T(H);
         V r;
-        r.x = H * (a.x - s * a.y);
-        r.y = H * (a.y + s * a.x);
+        r.x = h * (a.x - sgn<DIR>(a.y));
+        r.y = h * (a.y + sgn<DIR>(a.x));
         return r;
     } else if constexpr (J == 6) {  // H*(-1 + s i)
+        constexpr T h = T(H);
         V r;
-        r.x = -H * (a.x + s * a.y);
-        r.y = H * (s * a.x - a.y);
+        r.x = -(h * (a.x + sgn<DIR>(a.y)));
+        r.y = h * (sgn<DIR>(a.x) - a.y);
         return r;
     } else {
         static_assert(J == 1 || J == 3 || J == 9, "w16 exponent");
-        constexpr T cr = J == 1 ? C1 : (J == 3 ? S1 : -C1);
-        constexpr T ci = J == 1 ? s * S1 : (J == 3 ? s * C1 : -s * S1);
+        constexpr double crd = J == 1 ? C1 : (J == 3 ? S1 : -C1);
+        constexpr double cid = (double)DIR * (J == 1 ? S1 : (J == 3 ? C1 : -S1));
+        constexpr T cr = T(crd), ci = T(cid);
         V r;
         r.x = a.x * cr - a.y * ci;
         r.y = a.x * ci + a.y * cr;
@@ -123,21 +134,12 @@ __host__ __device__ __forceinline__ void dft4(V &v0, V &v1, V &v2, V &v3)
 template <int DIR, typename V>
 __host__ __device__ __forceinline__ void dft8(V *v)
 {
-    using T = decltype(v[0].x);
-    constexpr T H = (T)0.70710678118654752440;
-    constexpr T s = (T)DIR;
 #pragma unroll
     for (int n1 = 0; n1 < 4; n1++) dft2<DIR>(v[n1], v[n1 + 4]);
-    // w_8^n1 on the k0 = 1 half
-    {
-        V a = v[5];  // w_8 = H*(1 + s i)
-        v[5].x = H * (a.x - s * a.y);
-        v[5].y = H * (a.y + s * a.x);
-        v[6] = c_rot<DIR>(v[6]);
-        a = v[7];  // w_8^3 = H*(-1 + s i)
-        v[7].x = -H * (a.x + s * a.y);
-        v[7].y = H * (s * a.x - a.y);
-    }
+    // w_8^n1 on the k0 = 1 half (w_8 = w_16^2, w_8^3 = w_16^6)
+    v[5] = c_w16<DIR, 2>(v[5]);
+    v[6] = c_rot<DIR>(v[6]);
+    v[7] = c_w16<DIR, 6>(v[7]);
     dft4<DIR>(v[0], v[1], v[2], v[3]);
     dft4<DIR>(v[4], v[5], v[6], v[7]);
     V o[8];

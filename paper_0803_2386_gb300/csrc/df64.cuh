@@ -1,0 +1,126 @@
+// df64.cuh -- double-float arithmetic: a real number carried as the
+// unevaluated sum hi + lo of two floats (|lo| < ulp(hi)), about 48
+// significant bits, computed entirely on the FP32 pipes.
+//
+// GB300 executes FP64 at about 1/58 of its FP32 rate (measured), so an
+// FFT in native FP64 is bound by the FP64 issue rate at ~4 % of HBM.  The
+// double-float form keeps complex128 as the HBM format and the FP64 level of
+// accuracy (a few 1e-15 per operation) while running the butterflies in
+// FP32 instructions:
+//   sum:     Knuth's TwoSum of the high parts, plus the low parts, then a
+//            renormalising fast-two-sum (11 FP32 operations);
+//   product: the exact product of the high parts from one FMA (the rounding
+//            error of a*b is fma(a, b, -a*b)), plus the two cross terms,
+//            renormalised (7 operations).
+// The conversions at the HBM boundary -- double -> (hi, lo) on load and
+// (hi, lo) -> double on store -- are done with integer bit operations, so no
+// FP64 instruction is issued anywhere on the path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "codelets.cuh"
+
+namespace moafft {
+
+struct dfloat {
+    float hi, lo;
+    __host__ __device__ constexpr dfloat() : hi(0.f), lo(0.f) {}
+    __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    // rounding split of a double (host or compile-time constants only)
+    __host__ __device__ constexpr explicit dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return dfloat(s, b - (s - a));
+}
+
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return df_fast_two_sum(s, e);
+}
+
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b)
+{
+    const float p = a.hi * b.hi;
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+struct dcplx {
+    dfloat x, y;
+};
+
+template <> struct cvec<dfloat> { using type = dcplx; };
+
+// ---- HBM boundary: double <-> (hi, lo), integer operations only ---------
+
+// x = hi + lo with hi the first 24 significant bits of x and lo the next
+// (truncated to 24) bits: |hi + lo - x| < 2^-47 |x|.  Doubles outside the
+// normal float range become 0 (below 1.2e-38) or keep no low part.
+__device__ __forceinline__ dfloat df_from_double(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const int ef = e - 1023 + 127;
+    if (ef <= 0) return dfloat(__uint_as_float(sgn), __uint_as_float(sgn));
+    if (ef >= 255) return dfloat(__uint_as_float(sgn | 0x7f800000u), 0.f);  // overflow: infinity
+    const float hi = __uint_as_float(sgn | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
+    const uint32_t r = (uint32_t)(m & 0x1FFFFFFFull);  // the 29 bits below hi
+    if (r == 0) return dfloat(hi, 0.f);
+    const int p = 31 - __clz(r);            // leading one of r, 0..28
+    const int el = p + e - 1075 + 127;      // float exponent of lo
+    if (el <= 0) return dfloat(hi, 0.f);
+    const uint32_t frac = p <= 23 ? (r << (23 - p)) & 0x7FFFFFu : (r >> (p - 23)) & 0x7FFFFFu;
+    return dfloat(hi, __uint_as_float(sgn | ((uint32_t)el << 23) | frac));
+}
+
+// hi + lo rounded toward zero to a double (|lo| < ulp(hi) assumed, which
+// every operation above guarantees).
+__device__ __forceinline__ double df_to_double(dfloat v)
+{
+    const uint32_t bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
+    const int eh = (int)((bh >> 23) & 0xff);
+    if (eh == 0) return __longlong_as_double((long long)((unsigned long long)(bh >> 31) << 63));
+    if (eh == 0xff) return __longlong_as_double((long long)(((unsigned long long)(bh >> 31) << 63) | 0x7FF0000000000000ull));
+    long long m = (long long)((unsigned long long)((bh & 0x7FFFFFu) | 0x800000u) << 29);  // 53-bit significand
+    const int el = (int)((bl >> 23) & 0xff);
+    if (el != 0 && el != 0xff) {
+        const unsigned long long ml = (unsigned long long)((bl & 0x7FFFFFu) | 0x800000u);
+        const int sh = el - eh + 29;  // <= 6 when |lo| < ulp(hi)
+        long long L = 0;
+        if (sh >= 0) L = (long long)(ml << (sh < 8 ? sh : 8));
+        else if (sh > -40) L = (long long)(ml >> (-sh));
+        m += ((bh ^ bl) >> 31) ? -L : L;
+    }
+    int e = eh - 127 + 1023;
+    if (m >= (1ll << 53)) {
+        m >>= 1;
+        e += 1;
+    } else if (m < (1ll << 52)) {
+        m <<= 1;
+        e -= 1;
+    }
+    const unsigned long long bits = ((unsigned long long)(bh >> 31) << 63) | ((unsigned long long)e << 52) |
+                                    ((unsigned long long)m & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ dcplx dc_from(double2 a) { return dcplx{df_from_double(a.x), df_from_double(a.y)}; }
+__device__ __forceinline__ double2 dc_to(dcplx a) { return make_double2(df_to_double(a.x), df_to_double(a.y)); }
+
+}  // namespace moafft

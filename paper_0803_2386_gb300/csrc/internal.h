@@ -118,6 +118,12 @@ cudaError_t launch_twiddle_f64(double *dst, int64_t count, int64_t m, int64_t st
                                cudaStream_t s);
 cudaError_t launch_twiddle_f32(float *dst, int64_t count, int64_t m, int64_t stride,
                                cudaStream_t s);
+// double-float tables: each entry (re.hi, re.lo, im.hi, im.lo), 16 bytes
+cudaError_t launch_twiddle_df64(float *dst, int64_t count, int64_t m, int64_t stride, cudaStream_t s);
+// complex128 passes in double-float arithmetic (tiles_df64.cu); only tiles
+// of 2^4..2^12 points with the tile kernel's widths
+bool df64_covers(const PassArgs &a);
+cudaError_t launch_tile_df64(const PassArgs &a, int dir, cudaStream_t s);
 
 // threads per CTA for a pass
 int pass_threads(const PassArgs &a);

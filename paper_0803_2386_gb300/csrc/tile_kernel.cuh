@@ -32,7 +32,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "codelets.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace moafft {
@@ -52,6 +55,44 @@ __host__ __device__ constexpr int tile_min_blocks(int logr)
                : (sizeof(T) == 8 ? 512 : 768) / tile_threads(logr);
 }
 __device__ __forceinline__ int tpad(int pos) { return pos + (pos >> 4); }
+
+// How a scalar type meets memory: the element type in HBM (E), loads and
+// stores that convert between E and the register type V, weight-table
+// loads, and scaling by a power of two.  Identity for float and double;
+// for double-float the HBM element stays double2 (complex128) and the
+// weight tables hold (hi, lo) pairs.
+template <typename T> struct MemOf {
+    using V = typename cvec<T>::type;
+    using E = V;
+    static __device__ __forceinline__ V load(const E *p) { return *p; }
+    static __device__ __forceinline__ void store(E *p, V v) { *p = v; }
+    static __device__ __forceinline__ V ldg(const V *p) { return __ldg(p); }
+    // f: the scale already converted to the scalar type (once per thread)
+    static __device__ __forceinline__ T prep(double s) { return (T)s; }
+    static __device__ __forceinline__ void scale(V &v, T f)
+    {
+        v.x *= f;
+        v.y *= f;
+    }
+};
+template <> struct MemOf<dfloat> {
+    using V = dcplx;
+    using E = double2;
+    static __device__ __forceinline__ V load(const E *p) { return dc_from(*p); }
+    static __device__ __forceinline__ void store(E *p, V v) { *p = dc_to(v); }
+    static __device__ __forceinline__ V ldg(const V *p)
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        return dcplx{dfloat(t.x, t.y), dfloat(t.z, t.w)};
+    }
+    // the scale is a power of two: scaling both parts is exact
+    static __device__ __forceinline__ float prep(double s) { return (float)s; }
+    static __device__ __forceinline__ void scale(V &v, float f)
+    {
+        v.x = dfloat(v.x.hi * f, v.x.lo * f);
+        v.y = dfloat(v.y.hi * f, v.y.lo * f);
+    }
+};
 
 // true when the compile-time tile kernel covers this pass
 inline bool tile_covers(const PassArgs &a)
@@ -159,7 +200,8 @@ __device__ __forceinline__ void tile_load(const PassArgs &p, const TileRef &r, t
     const int u = tid / W;
     const int64_t n = p.n;
     (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
-    const V *in = reinterpret_cast<const V *>(p.in);
+    using M = MemOf<T>;
+    const typename M::E *in = reinterpret_cast<const typename M::E *>(p.in);
     const int64_t mstride = LAST ? 1 : p.B;
     const int64_t base = r.base;
     const bool valid = r.valid;
@@ -169,8 +211,8 @@ __device__ __forceinline__ void tile_load(const PassArgs &p, const TileRef &r, t
 #pragma unroll
         for (int e = 0; e < E0; e++) {
             const int m = e * Q0 + g * U + u;
-            if (valid) v[g * E0 + e] = in[base + (int64_t)m * mstride];
-            else { v[g * E0 + e].x = 0; v[g * E0 + e].y = 0; }
+            if (valid) v[g * E0 + e] = M::load(in + base + (int64_t)m * mstride);
+            else { v[g * E0 + e].x = T(0.0); v[g * E0 + e].y = T(0.0); }
         }
 
 }
@@ -194,8 +236,9 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     const int u = tid / W;
     const int64_t n = p.n;
     (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
+    using M = MemOf<T>;
     const V *twt = reinterpret_cast<const V *>(p.tw_tile);
-    V *out = reinterpret_cast<V *>(p.out);
+    typename M::E *out = reinterpret_cast<typename M::E *>(p.out);
     const int64_t sbase = r.sbase, b0 = r.b0, tr = r.tr, vrow = r.vrow;
     const bool valid = r.valid;
     (void)tr;
@@ -206,7 +249,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
         if constexpr (NS > 1) {
             const int mq = g * U + u;
 #pragma unroll
-            for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], __ldg(twt + mq * k));
+            for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twt + mq * k));
         }
     }
 
@@ -218,7 +261,10 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + g * U + u) * W + w] = v[g * E0 + k];
         __syncthreads();
         int S = Q0;
-#pragma unroll
+        // one copy of the radix-16 digit's code for double-float, whose
+        // unrolled codelets would overflow the instruction cache
+        constexpr int kUnroll = std::is_same<T, dfloat>::value ? 1 : 4;
+#pragma unroll kUnroll
         for (int j = 1; j < NS; j++) {
             const int Q = S / 16;
             const int pre = u / Q, mq = u % Q;
@@ -230,7 +276,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
                 if (mq != 0) {
                     const int step = R / S;
 #pragma unroll
-                    for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], __ldg(twt + mq * k * step));
+                    for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twt + mq * k * step));
                 }
                 // each thread rewrites exactly the positions it read
 #pragma unroll
@@ -275,28 +321,28 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             if (ex != 0) {
                 V wv;
                 if (p.tw_lo_bits == 0) {
-                    wv = __ldg(reinterpret_cast<const V *>(p.tw_pass) + ex);
+                    wv = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + ex);
                 } else {
-                    const V wa = __ldg(reinterpret_cast<const V *>(p.tw_pass) +
-                                       (ex & ((((int64_t)1) << p.tw_lo_bits) - 1)));
-                    const V wb = __ldg(reinterpret_cast<const V *>(p.tw_hi) + (ex >> p.tw_lo_bits));
+                    const V wa = M::ldg(reinterpret_cast<const V *>(p.tw_pass) +
+                                        (ex & ((((int64_t)1) << p.tw_lo_bits) - 1)));
+                    const V wb = M::ldg(reinterpret_cast<const V *>(p.tw_hi) + (ex >> p.tw_lo_bits));
                     wv = c_mul(wa, wb);
                 }
                 x = c_tw<DIR>(x, wv);
             }
-            out[sbase + (int64_t)kk * p.B] = x;
+            M::store(out + sbase + (int64_t)kk * p.B, x);
         }
     } else {
         const int64_t obase = sbase + vrow;
         const int64_t kstride = n / R;
-        const T sc = (T)p.scale;
         const bool scale = p.scale != 1.0;
+        const auto sf = M::prep(p.scale);
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int kk = revu + U * j;
             V x = v[j];
-            if (scale) { x.x *= sc; x.y *= sc; }
-            out[obase + (int64_t)kk * kstride] = x;
+            if (scale) M::scale(x, sf);
+            M::store(out + obase + (int64_t)kk * kstride, x);
         }
     }
 }

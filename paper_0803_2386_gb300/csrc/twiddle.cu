@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
 #include "internal.h"
 
 namespace moafft {
@@ -34,6 +35,19 @@ __global__ void twiddle_f32_kernel(float2 *dst, int64_t count, int64_t m, int64_
     }
 }
 
+// double-float weights: the FP64 value split into (hi, lo) float pairs
+__global__ void twiddle_df64_kernel(float4 *dst, int64_t count, int64_t m, int64_t stride)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (j * stride) % m;
+        double s, c;
+        sincospi(2.0 * (double)e / (double)m, &s, &c);
+        const dfloat re(c), im(-s);
+        dst[j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+
 static int grid_for(int64_t count)
 {
     int64_t g = (count + 255) / 256;
@@ -57,6 +71,13 @@ cudaError_t launch_twiddle_f32(float *dst, int64_t count, int64_t m, int64_t str
     if (count <= 0) return cudaSuccess;
     twiddle_f32_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<float2 *>(dst), count,
                                                         m, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle_df64(float *dst, int64_t count, int64_t m, int64_t stride, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    twiddle_df64_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<float4 *>(dst), count, m, stride);
     return cudaGetLastError();
 }
 

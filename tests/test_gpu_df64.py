@@ -1,0 +1,86 @@
+"""Double-float form: complex128 transforms whose butterflies run in
+double-float arithmetic (pairs of floats, ~48 significant bits) on the FP32
+pipes.  Same tolerance as the FP64 path: relative L2 <= 1e-12 against the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_0803_2386_gb300 as M
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    M.build()
+    yield
+
+
+def rel_rows(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def run(x, direction=M.FFT_FORWARD, adjoint=False, inplace=False, rows=None):
+    batch, n = x.shape
+    d_in = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    d_out = d_in if inplace else torch.empty_like(d_in)
+    p = M.fft_plan_ex(n, batch, M.FFT_C128, direction, M.FFT_FORM_DF64)
+    try:
+        (M.fft_exec_adjoint if adjoint else M.fft_exec)(p, d_in, d_out)
+        M.fft_plan_check(p)
+        assert '"form": "df64"' in M.fft_plan_describe(p)
+    finally:
+        M.fft_destroy(p)
+    out = d_out if rows is None else d_out[rows]
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("t", [4, 5, 8, 10, 11, 12, 13, 16])
+def test_df64_sizes(t):
+    n = 1 << t
+    x = W.uniform_complex(n, 3, seed=300 + t)
+    for direction, op in ((M.FFT_FORWARD, "forward"), (M.FFT_INVERSE, "inverse")):
+        err = rel_rows(run(x, direction), O.fft(x, op, c=64))
+        assert err.max() <= 1e-12, (t, op, err.max())
+    err = rel_rows(run(x, M.FFT_INVERSE, adjoint=True), O.fft(x, "adjoint_inverse", c=64))
+    assert err.max() <= 1e-12
+    err = rel_rows(run(x, inplace=True), O.fft(x, "forward", c=64))
+    assert err.max() <= 1e-12
+
+
+def test_df64_closed_forms_n1024():
+    n = 1024
+    k = np.arange(n)
+    cf = W.closed_form_inputs(n)
+    X = np.stack([cf[key] for key in ("delta0", "delta5", "const", "cos37")])
+    Y = run(X)
+    exact = np.zeros((4, n), complex)
+    exact[0] = 1.0
+    exact[1] = np.exp(-2j * np.pi * ((5 * k) % n) / n)
+    exact[2, 0] = n
+    exact[3, 37] = exact[3, n - 37] = n / 2
+    assert np.abs(Y - exact).max() < 1e-11 * n
+
+
+def test_df64_full_size_sampled():
+    n, batch = 1 << 20, 64
+    x = W.uniform_complex(n, batch, seed=0)
+    picks = [0, 33, 63]
+    y = run(x, rows=picks)
+    ref = O.fft(x[picks], "forward", c=1024, threads=3)
+    assert rel_rows(y, ref).max() <= 1e-12
+
+
+def test_df64_rejects_small_and_c64():
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan_ex(8, 1, M.FFT_C128, M.FFT_FORWARD, M.FFT_FORM_DF64)
+    assert e.value.status == M.FFT_ERR_UNSUPPORTED
+    with pytest.raises(M.MoaFFTError) as e:
+        M.fft_plan_ex(1024, 1, M.FFT_C64, M.FFT_FORWARD, M.FFT_FORM_DF64)
+    assert e.value.status == M.FFT_ERR_UNSUPPORTED
