@@ -327,6 +327,7 @@ def run_moafft(args):
     e2e = None
     if args.e2e_steps > 0:
         e2e = measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, world, args)
+    forms = measure_forms(M, torch, x, X, stream, n, batch, world, args) if rank == 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -334,7 +335,8 @@ def run_moafft(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded uniform[-1,1], seed = rank)",
                 "config": config(n, batch, world), "gpu_launches": launches,
-                "roundtrip_rel_err": rt, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+                "roundtrip_rel_err": rt, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+                "forms": forms}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(n, batch)
         print(json.dumps(line), flush=True)
@@ -349,6 +351,30 @@ def run_moafft(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_forms(M, torch, x, X, stream, n, batch, world, args):
+    """The same step (forward + inverse of this batch) in the library's other
+    complex128 form: double-float butterflies on the FP32 pipes.  Its error
+    is relative L2 against the FP64 path's spectrum X (computed above)."""
+    if n < 16:
+        return None
+    y = torch.empty_like(x)
+    r = torch.empty_like(x)
+    pf = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD, M.FFT_FORM_DF64)
+    pi = M.Plan(n, batch, M.FFT_C128, M.FFT_INVERSE, M.FFT_FORM_DF64)
+
+    def step():
+        pf.exec(x, y, stream)
+        pi.exec(y, r, stream)
+
+    ms = _time(torch, stream, step, max(1, args.steps), warm=2)
+    err = (torch.linalg.vector_norm((y - X).flatten()) / torch.linalg.vector_norm(X.flatten())).item()
+    pf.close()
+    pi.close()
+    return {"df64": {"value": round(flops_per_step(n, batch) * world / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+                     "ms_per_step": round(ms, 4), "dtype": "f32x2 (double-float)",
+                     "rel_err_vs_fp64_path": err, "tolerance": 1e-12}}
 
 
 def measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, world, args):
