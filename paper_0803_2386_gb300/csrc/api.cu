@@ -166,10 +166,21 @@ static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
         split_subpasses(p);
         p.tw_m = R * p.B;
         p.tw_lo_bits = 0;
+        p.tw_mode = 0;
         if (!last) {
-            int lm = exact_log2(p.tw_m);
-            int direct_max = dt == FFT_C128 ? 20 : 12;
-            if (lm > direct_max) p.tw_lo_bits = (lm + 1) / 2;
+            // rows of the table follow the tile index k, so a warp's
+            // consecutive columns b read consecutive weights: the whole
+            // table (mode 2) up to 2^20 (complex128: FP64-bound passes, an
+            // extra complex product costs more than the table's L2 reads) /
+            // 2^12 (complex64: measured, the two small tables of the digit
+            // split stay in L1) entries, else split by the digits of k
+            // (mode 3), else (passes of < 16 points) the two-level table
+            // indexed by b k
+            const int lm = exact_log2(p.tw_m);
+            const int direct_max = dt == FFT_C128 ? 20 : 12;
+            if (lm <= direct_max) p.tw_mode = 2;
+            else if (p.log_r >= 4) p.tw_mode = 3;
+            else p.tw_lo_bits = (lm + 1) / 2;
         }
     }
     return FFT_OK;
@@ -239,6 +250,14 @@ static int build_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
         if (chunk) *chunk = k;
     }
     if (body.empty() || body == "auto") return default_schedule(s, n, dt);
+    if (body == "cluster") {
+        if (dt != FFT_C64 || n != ((int64_t)1 << cluster_log2n()))
+            return fail(FFT_ERR_UNSUPPORTED, "schedule 'cluster' takes complex64 transforms of n = 2^%d",
+                        cluster_log2n());
+        int st = default_schedule(s, n, dt);
+        s.cluster = true;
+        return st;
+    }
     if (body == "stages") {
         s = Schedule();
         s.n = n;
@@ -255,7 +274,7 @@ static std::string schedule_json(const Schedule &s)
     if (s.unblocked)
         return "{\"n\": " + std::to_string(s.n) + ", \"unblocked\": true, \"stages\": " + std::to_string(s.t) +
                ", \"passes\": []}";
-    std::string j = "{\"n\": " + std::to_string(s.n) + ", \"passes\": [";
+    std::string j = "{\"n\": " + std::to_string(s.n) + (s.cluster ? ", \"cluster\": true" : "") + ", \"passes\": [";
     for (int i = 0; i < s.npass; i++) {
         const PassDesc &p = s.pass[i];
         char buf[256];
@@ -263,9 +282,9 @@ static std::string schedule_json(const Schedule &s)
         for (int k = 0; k < p.nsub; k++) subs += (k ? "," : "") + std::to_string(p.sub_log[k]);
         snprintf(buf, sizeof buf,
                  "%s{\"log_r\": %d, \"A\": %lld, \"B\": %lld, \"width\": %d, \"sub_log\": [%s], "
-                 "\"tw_m\": %lld, \"tw_lo_bits\": %d}",
+                 "\"tw_m\": %lld, \"tw_lo_bits\": %d, \"tw_mode\": %d}",
                  i ? ", " : "", p.log_r, (long long)p.A, (long long)p.B, p.width, subs.c_str(),
-                 (long long)p.tw_m, p.tw_lo_bits);
+                 (long long)p.tw_m, p.tw_lo_bits, p.tw_mode);
         j += buf;
     }
     j += "]}";
@@ -285,6 +304,7 @@ static std::vector<std::string> tune_candidates(int64_t n, fft_dtype dt)
 {
     std::vector<std::string> out;
     const int t = exact_log2(n);
+    if (dt == FFT_C64 && t == cluster_log2n()) out.push_back("cluster");
     if (t <= 12) {
         out.push_back(std::to_string(t));
         if (t >= 8)
@@ -470,7 +490,7 @@ size_t pass_smem_bytes(const PassArgs &a, size_t eb)
 static int64_t class_launches(const SizeClass &c)
 {
     if (c.sched.unblocked) return 1 + c.sched.t;
-    if (c.sched.npass == 1) return 1;
+    if (c.sched.npass == 1 || (c.sched.cluster && c.offs.empty())) return 1;
     return (c.count + c.chunk - 1) / c.chunk * c.sched.npass;
 }
 
@@ -493,14 +513,23 @@ static int make_tables(fft_plan_s *p)
             c.sched.pass[0].tw_pass_off = off;
             off += (size_t)std::max<int64_t>(1, c.n / 2);
         }
+        if (c.sched.cluster) {
+            c.sched.tw_direct_off = off;
+            off += (size_t)c.n;
+        }
         for (int i = 0; i < c.sched.npass; i++) {
             PassDesc &d = c.sched.pass[i];
             d.tw_tile_off = off;
             off += (size_t)1 << d.log_r;
             if (i < c.sched.npass - 1) {
                 d.tw_pass_off = off;
-                if (d.tw_lo_bits == 0) off += (size_t)d.tw_m;
-                else {
+                if (d.tw_mode == 3) {
+                    off += (size_t)(((int64_t)1 << (d.log_r - 4)) * d.B);
+                    d.tw_hi_off = off;
+                    off += (size_t)(16 * d.B);
+                } else if (d.tw_lo_bits == 0) {
+                    off += (size_t)d.tw_m;
+                } else {
                     off += (size_t)1 << d.tw_lo_bits;
                     d.tw_hi_off = off;
                     off += (size_t)(d.tw_m >> d.tw_lo_bits);
@@ -511,6 +540,10 @@ static int make_tables(fft_plan_s *p)
     int st = dev_alloc(p->tw, off * eb, "twiddle tables");
     if (st != FFT_OK) return st;
     for (auto &c : p->classes) {
+        if (c.sched.cluster) {
+            cudaError_t e = launch_twiddle_f32((float *)p->tw.ptr + 2 * c.sched.tw_direct_off, c.n, c.n, 1, 0);
+            if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
+        }
         if (c.sched.unblocked && c.n > 1) {
             cudaError_t e = p->dt == FFT_C128
                                 ? launch_twiddle_f64((double *)p->tw.ptr + 2 * c.sched.pass[0].tw_pass_off, c.n / 2,
@@ -529,9 +562,18 @@ static int make_tables(fft_plan_s *p)
                     return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
                 return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
             };
+            const int kind = p->form == FFT_FORM_DF64 ? 2 : (p->dt == FFT_C128 ? 0 : 1);
+            const size_t wb = p->form == FFT_FORM_DF64 ? 16 : eb;
+            char *arena = (char *)p->tw.ptr;
             cudaError_t e = gen(d.tw_tile_off, R, R, 1);
             if (e == cudaSuccess && i < c.sched.npass - 1) {
-                if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
+                if (d.tw_mode == 2) {
+                    e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, R, d.B, d.tw_m, 1, 0);
+                } else if (d.tw_mode == 3) {
+                    const int64_t U = (int64_t)1 << (d.log_r - 4);
+                    e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, U, d.B, d.tw_m, 1, 0);
+                    if (e == cudaSuccess) e = launch_twiddle_2d(arena + d.tw_hi_off * wb, kind, 16, d.B, d.tw_m, U, 0);
+                } else if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
                 else {
                     e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
                     if (e == cudaSuccess)
@@ -605,6 +647,9 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
             ws = std::max<int64_t>(ws, c.count * c.n * (int64_t)eb);  // for in-place calls
         } else if (c.sched.npass > 1) {
             c.chunk = std::max<int64_t>(1, std::min<int64_t>(c.count, target / (c.n * (int64_t)eb)));
+            // one-launch cluster plans keep a small workspace for the two-pass
+            // fallback (buffers the tensor map cannot describe)
+            if (c.sched.cluster && c.offs.empty()) c.chunk = std::min<int64_t>(c.count, 16);
             if (req_chunk > 0) c.chunk = std::min<int64_t>(c.count, req_chunk);
             ws = std::max<int64_t>(ws, c.chunk * c.n * (int64_t)eb);
         } else {
@@ -674,6 +719,8 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     c.count = batch;
     int64_t req_chunk = 0;
     st = build_schedule(c.sched, n, dt, schedule, &req_chunk);
+    if (st == FFT_OK && c.sched.cluster && form != FFT_FORM_PLAIN)
+        st = fail(FFT_ERR_UNSUPPORTED, "schedule 'cluster' runs the plain complex64 form only");
     if (st == FFT_OK && form == FFT_FORM_DF64) {
         bool ok = !c.sched.unblocked && c.sched.npass > 0;
         for (int i = 0; ok && i < c.sched.npass; i++) {
@@ -770,6 +817,7 @@ static void fill_args(const fft_plan_s *p, const SizeClass &C, int i, PassArgs &
     a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
     a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
     a.tw_lo_bits = d.tw_lo_bits;
+    a.tw_mode = d.tw_mode;
     a.scale = a.is_last && p->dir == FFT_INVERSE ? 1.0 / (double)C.n : 1.0;
     a.err = (int *)p->err.ptr;
 }
@@ -943,6 +991,29 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
         if (e != cudaSuccess) return fail_cuda(e, "per-stage launch");
         return FFT_OK;
     }
+    if (S.cluster && !ragged) {
+        const char *src = (const char *)in + (size_t)t0 * C.n * eb;
+        char *dst = (char *)out + (size_t)t0 * C.n * eb;
+        fft_plan_s::Rec rec{0, nullptr, nullptr};
+        if (p->profile) {
+            rec.a = take_event(p);
+            rec.b = take_event(p);
+            if (rec.a) cudaEventRecord(rec.a, s);
+        }
+        cudaError_t e = launch_cluster_f32(src, dst, cnt, (const char *)p->tw.ptr + S.tw_direct_off * eb, scale,
+                                           (int *)p->err.ptr, sign, s);
+        if (e == cudaSuccess) {
+            if (p->profile && rec.a && rec.b) {
+                cudaEventRecord(rec.b, s);
+                p->recs.push_back(rec);
+            }
+            return FFT_OK;
+        }
+        if (rec.a) p->ev_free.push_back(rec.a);
+        if (rec.b) p->ev_free.push_back(rec.b);
+        if (e != cudaErrorNotSupported) return fail_cuda(e, "cluster launch");
+        cudaGetLastError();  // the two-pass path below
+    }
     PassArgs a;
     memset(&a, 0, sizeof a);
     a.n = C.n;
@@ -972,6 +1043,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
             a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
             a.tw_lo_bits = d.tw_lo_bits;
+            a.tw_mode = d.tw_mode;
             a.scale = a.is_last ? scale : 1.0;
             a.err = (int *)p->err.ptr;
             a.tc_dft = p->tcf.ptr ? (const char *)p->tcf.ptr + (sign < 0 ? 0 : 4096) : nullptr;
@@ -1359,6 +1431,9 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
     if (p->classes.size() == 1) {
         j += ", \"chunk\": " + std::to_string(p->classes[0].chunk) + ", \"schedule\": " +
              schedule_json(p->classes[0].sched);
+        if (p->classes[0].sched.cluster)
+            j += ", \"resident_clusters\": " + std::to_string(cluster_max_active()) +
+                 ", \"cluster_ctas\": " + std::to_string(cluster_ctas());
     }
     j += ", \"classes\": [";
     for (size_t i = 0; i < p->classes.size(); i++) {

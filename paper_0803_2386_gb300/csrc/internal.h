@@ -27,7 +27,8 @@ struct PassDesc {
     int nsub = 0;                // register-level sub-passes inside the tile
     int sub_log[kMaxSub] = {0};  // log2 radix of each sub-pass, top digit first
     int64_t A = 1, B = 1;        // n = A * R * B
-    int tw_lo_bits = 0;          // 0: direct pass-twiddle table, else two-level
+    int tw_lo_bits = 0;          // mode 0: 0 = direct table, else two-level
+    int tw_mode = 0;             // pass-weight table layout (PassArgs::tw_mode)
     int64_t tw_m = 1;            // M = R*B: pass twiddles are w_M^e
     size_t tw_tile_off = 0;      // element offsets into the plan's twiddle arena
     size_t tw_pass_off = 0;
@@ -43,6 +44,13 @@ struct Schedule {
     // stage after a bit-reversal pass (stages.cu); pass[0].tw_pass_off then
     // locates the table w_n^e, e < n/2
     bool unblocked = false;
+    // schedule "cluster" (complex64, n = 2^16): one launch whose 8-CTA
+    // clusters keep a whole transform in distributed shared memory
+    // (cluster_kernel.cu); pass[0].tw_pass_off then locates the direct table
+    // w_n^e, e < n.  The passes stay filled in (the 8,8 split) for the
+    // two-pass fallback.
+    bool cluster = false;
+    size_t tw_direct_off = 0;
 };
 
 // Parameters of one pass launch (passed by value to the kernel).
@@ -60,9 +68,18 @@ struct PassArgs {
     int npass;                  // passes of the whole schedule
     int pass_log[kMaxPasses];   // their log2 radices (for the final transpose)
     const void *tw_tile;        // w_R^e, e < R
-    const void *tw_pass;        // w_M^e (direct) or w_M^e, e < 2^lo_bits (two-level)
-    const void *tw_hi;          // w_M^(e << lo_bits) (two-level)
+    // Pass weights w_M^(b k), M = R B, b < B the column, k < R the tile
+    // index, in one of these layouts (tw_mode):
+    //   0: indexed by e = b k: tw_pass = w_M^e (tw_lo_bits = 0) or the
+    //      two-level pair tw_pass = w_M^e, e < 2^lo_bits, tw_hi =
+    //      w_M^(e << lo_bits);
+    //   2: rows by k: tw_pass[k B + b] (a warp's columns are consecutive);
+    //   3: rows by the digits of k = r + U j, U = R / 16: tw_pass[r B + b] =
+    //      w_M^(b r), tw_hi[j B + b] = w_M^(b U j).
+    const void *tw_pass;
+    const void *tw_hi;
     int tw_lo_bits;
+    int tw_mode;
     double scale;               // applied in the last pass (1 or 1/n)
     // ragged batches: element offset of transform tr in `in` (loads) and in
     // `out` (stores); NULL means the dense layout tr * n
@@ -101,6 +118,16 @@ cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total
 cudaError_t launch_stages(bool f64, const void *in, void *out, void *tmp, int64_t n, int64_t count, const void *tw,
                           int dir, double scale, cudaStream_t s);
 
+// one-round-trip complex64 transforms of n = 2^cluster_log2n() through
+// thread-block clusters (cluster_kernel.cu); cudaErrorNotSupported when the
+// device or the buffers do not allow it
+int cluster_log2n();
+bool cluster_available();
+int cluster_max_active();  // clusters resident at once (0: none)
+int cluster_ctas();        // CTAs per cluster (16, or 8 when 16 does not fit)
+cudaError_t launch_cluster_f32(const void *in, void *out, int64_t count, const void *tw, double scale, int *err,
+                               int dir, cudaStream_t s);
+
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);
 cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);
@@ -120,6 +147,10 @@ cudaError_t launch_twiddle_f32(float *dst, int64_t count, int64_t m, int64_t str
                                cudaStream_t s);
 // double-float tables: each entry (re.hi, re.lo, im.hi, im.lo), 16 bytes
 cudaError_t launch_twiddle_df64(float *dst, int64_t count, int64_t m, int64_t stride, cudaStream_t s);
+// 2-D tables dst[r cols + c] = exp(-2*pi*i * (r*rstep*c mod m) / m), r < rows,
+// c < cols; kind 0 complex128, 1 complex64, 2 double-float pairs
+cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, int64_t m, int64_t rstep,
+                              cudaStream_t s);
 // complex128 passes in double-float arithmetic (tiles_df64.cu); only tiles
 // of 2^4..2^12 points with the tile kernel's widths
 bool df64_covers(const PassArgs &a);

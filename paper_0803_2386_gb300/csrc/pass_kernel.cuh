@@ -66,16 +66,22 @@ __device__ __forceinline__ int64_t unrev_rows(int64_t v, const PassArgs &p)
     return a;
 }
 
+// the pass weight w_M^(b k) in the plan's table layout (PassArgs::tw_mode;
+// the digit split, mode 3, is only chosen for passes of >= 16 points)
 template <typename T, int DIR>
-__device__ __forceinline__ typename cvec<T>::type pass_weight(const PassArgs &p, int64_t e)
+__device__ __forceinline__ typename cvec<T>::type pass_weight(const PassArgs &p, int64_t b, int k)
 {
     using V = typename cvec<T>::type;
-    const V *lo = reinterpret_cast<const V *>(p.tw_pass);
-    if (p.tw_lo_bits == 0) return __ldg(lo + e);
-    const V *hi = reinterpret_cast<const V *>(p.tw_hi);
-    V a = __ldg(lo + (e & ((((int64_t)1) << p.tw_lo_bits) - 1)));
-    V b = __ldg(hi + (e >> p.tw_lo_bits));
-    return c_mul(a, b);
+    const V *t0 = reinterpret_cast<const V *>(p.tw_pass);
+    const V *t1 = reinterpret_cast<const V *>(p.tw_hi);
+    if (p.tw_mode == 2) return __ldg(t0 + (int64_t)k * p.B + b);
+    if (p.tw_mode == 3) {
+        const int ul = p.log_r - 4;
+        return c_mul(__ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * p.B + b), __ldg(t1 + (int64_t)(k >> ul) * p.B + b));
+    }
+    const int64_t e = b * (int64_t)k;
+    if (p.tw_lo_bits == 0) return __ldg(t0 + e);
+    return c_mul(__ldg(t0 + (e & ((((int64_t)1) << p.tw_lo_bits) - 1))), __ldg(t1 + (e >> p.tw_lo_bits)));
 }
 
 // One register sub-pass of radix 2^LE over the whole tile (all W columns).
@@ -155,8 +161,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
         for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
             int w = idx % W, k = idx / W;
             V v = tile[spad(tile_pos(k, p) * W + w)];
-            int64_t e = (b0 + w) * (int64_t)k;  // w_{R*B}^(b*k)
-            if (e != 0) v = c_tw<DIR>(v, pass_weight<T, DIR>(p, e));
+            if (b0 + w != 0 && k != 0) v = c_tw<DIR>(v, pass_weight<T, DIR>(p, b0 + w, k));  // w_{R*B}^(b*k)
             out[sbase + (int64_t)k * p.B + w] = v;
         }
     } else {

@@ -348,21 +348,17 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) tc_tile_kernel(PassArgs
     if (!valid) return;
     if constexpr (!LAST) {
         const int64_t b = b0 + w;
+        // digit-split weights (k = revu + U j): this thread's factor once
+        const V wr = p.tw_mode == 3 ? __ldg(reinterpret_cast<const V *>(p.tw_pass) + (int64_t)revu * p.B + b)
+                                    : make_float2(1.f, 0.f);
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int kk = revu + U * j;
             V x = v[j];
-            const int64_t ex = b * (int64_t)kk;
-            if (ex != 0) {
-                V wv;
-                if (p.tw_lo_bits == 0) {
-                    wv = __ldg(reinterpret_cast<const V *>(p.tw_pass) + ex);
-                } else {
-                    const V wa = __ldg(reinterpret_cast<const V *>(p.tw_pass) +
-                                       (ex & ((((int64_t)1) << p.tw_lo_bits) - 1)));
-                    const V wb = __ldg(reinterpret_cast<const V *>(p.tw_hi) + (ex >> p.tw_lo_bits));
-                    wv = c_mul(wa, wb);
-                }
+            if (b != 0 && kk != 0) {
+                const V wv = p.tw_mode == 3
+                                 ? c_mul(wr, __ldg(reinterpret_cast<const V *>(p.tw_hi) + (int64_t)j * p.B + b))
+                                 : pass_weight_at<float>(p, b, kk);
                 x = c_tw<DIR>(x, wv);
             }
             out[sbase + (int64_t)kk * p.B] = x;

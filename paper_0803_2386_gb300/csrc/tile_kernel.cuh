@@ -94,6 +94,25 @@ template <> struct MemOf<dfloat> {
     }
 };
 
+// The pass weight w_M^(b k) for column b and tile index k in the plan's
+// table layout (PassArgs::tw_mode); (b, k) with b k = 0 need no weight.
+template <typename T>
+__device__ __forceinline__ typename cvec<T>::type pass_weight_at(const PassArgs &p, int64_t b, int k)
+{
+    using V = typename cvec<T>::type;
+    using M = MemOf<T>;
+    const V *t0 = reinterpret_cast<const V *>(p.tw_pass);
+    const V *t1 = reinterpret_cast<const V *>(p.tw_hi);
+    if (p.tw_mode == 2) return M::ldg(t0 + (int64_t)k * p.B + b);
+    if (p.tw_mode == 3) {
+        const int ul = p.log_r - 4;
+        return c_mul(M::ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * p.B + b), M::ldg(t1 + (int64_t)(k >> ul) * p.B + b));
+    }
+    const int64_t ex = b * (int64_t)k;
+    if (p.tw_lo_bits == 0) return M::ldg(t0 + ex);
+    return c_mul(M::ldg(t0 + (ex & ((((int64_t)1) << p.tw_lo_bits) - 1))), M::ldg(t1 + (ex >> p.tw_lo_bits)));
+}
+
 // true when the compile-time tile kernel covers this pass
 inline bool tile_covers(const PassArgs &a)
 {
@@ -313,24 +332,26 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     if (!valid) return;
     if constexpr (!LAST) {
         const int64_t b = b0 + w;
+        if (p.tw_mode == 3) {
+            // k = revu + U j: the digit-r factor w_M^(b revu) is this
+            // thread's, the rest is one row of the second table per j
+            const V *t1 = reinterpret_cast<const V *>(p.tw_hi) + b;
+            const V wr = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + (int64_t)revu * p.B + b);
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int kk = revu + U * j;  // NS == 1: R = 16, U = 1, revu = 0
-            V x = v[j];
-            const int64_t ex = b * (int64_t)kk;
-            if (ex != 0) {
-                V wv;
-                if (p.tw_lo_bits == 0) {
-                    wv = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + ex);
-                } else {
-                    const V wa = M::ldg(reinterpret_cast<const V *>(p.tw_pass) +
-                                        (ex & ((((int64_t)1) << p.tw_lo_bits) - 1)));
-                    const V wb = M::ldg(reinterpret_cast<const V *>(p.tw_hi) + (ex >> p.tw_lo_bits));
-                    wv = c_mul(wa, wb);
-                }
-                x = c_tw<DIR>(x, wv);
+            for (int j = 0; j < 16; j++) {
+                const int kk = revu + U * j;
+                V x = v[j];
+                if (b != 0 && kk != 0) x = c_tw<DIR>(x, c_mul(wr, M::ldg(t1 + (int64_t)j * p.B)));
+                M::store(out + sbase + (int64_t)kk * p.B, x);
             }
-            M::store(out + sbase + (int64_t)kk * p.B, x);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int kk = revu + U * j;  // NS == 1: R = 16, U = 1, revu = 0
+                V x = v[j];
+                if (b != 0 && kk != 0) x = c_tw<DIR>(x, pass_weight_at<T>(p, b, kk));
+                M::store(out + sbase + (int64_t)kk * p.B, x);
+            }
         }
     } else {
         const int64_t obase = sbase + vrow;

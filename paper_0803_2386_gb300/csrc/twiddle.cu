@@ -48,6 +48,26 @@ __global__ void twiddle_df64_kernel(float4 *dst, int64_t count, int64_t m, int64
     }
 }
 
+__global__ void twiddle_2d_kernel(void *dst, int kind, int64_t rows, int64_t cols, int64_t m, int64_t rstep)
+{
+    const int64_t count = rows * cols;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = j / cols, c = j - r * cols;
+        const int64_t e = ((r * rstep) % m) * c % m;
+        double s, co;
+        sincospi(2.0 * (double)e / (double)m, &s, &co);
+        if (kind == 0) {
+            reinterpret_cast<double2 *>(dst)[j] = make_double2(co, -s);
+        } else if (kind == 1) {
+            reinterpret_cast<float2 *>(dst)[j] = make_float2((float)co, (float)-s);
+        } else {
+            const dfloat re(co), im(-s);
+            reinterpret_cast<float4 *>(dst)[j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+}
+
 static int grid_for(int64_t count)
 {
     int64_t g = (count + 255) / 256;
@@ -78,6 +98,14 @@ cudaError_t launch_twiddle_df64(float *dst, int64_t count, int64_t m, int64_t st
 {
     if (count <= 0) return cudaSuccess;
     twiddle_df64_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<float4 *>(dst), count, m, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, int64_t m, int64_t rstep,
+                              cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    twiddle_2d_kernel<<<grid_for(rows * cols), 256, 0, s>>>(dst, kind, rows, cols, m, rstep);
     return cudaGetLastError();
 }
 

@@ -135,3 +135,16 @@ def test_tune_candidates_are_valid_schedules(t, dt):
 def test_unblocked_schedule_describes_stages():
     s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "stages"))
     assert s["unblocked"] and s["stages"] == 12 and s["passes"] == []
+
+
+def test_cluster_schedule_describes_two_groups():
+    """Schedule "cluster" (complex64, n = 2^16): the 8,8 split whose
+    reshape-transpose goes through distributed shared memory."""
+    s = json.loads(M.fft_describe_schedule(1 << 16, M.FFT_C64, M.FFT_FORM_PLAIN, "cluster"))
+    assert s["cluster"] is True and [p["log_r"] for p in s["passes"]] == [8, 8]
+    for n, dt in [(1 << 15, M.FFT_C64), (1 << 16, M.FFT_C128), (1 << 17, M.FFT_C64)]:
+        with pytest.raises(M.MoaFFTError) as e:
+            M.fft_describe_schedule(n, dt, M.FFT_FORM_PLAIN, "cluster")
+        assert e.value.status == M.FFT_ERR_UNSUPPORTED
+    assert "cluster" in M.fft_tune_candidates(1 << 16, M.FFT_C64)
+    assert "cluster" not in M.fft_tune_candidates(1 << 16, M.FFT_C128)
