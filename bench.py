@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c64", "c64_cluster", "tc_fp16", "tc_bf16", "c128", "df64"],
+    ap.add_argument("--case", default="", choices=["", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -627,8 +627,14 @@ def run_case(args):
     import torch
     import paper_0803_2386_gb300 as M
     form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
-            "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN}[args.case]
-    if args.case in ("c128", "df64"):
+            "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN,
+            "c64_rows": M.FFT_FORM_PLAIN}[args.case]
+    if args.case == "c64_rows":  # single-pass transforms (row tiles only)
+        n, batch = 1 << 10, 1 << 16
+        x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form)
+    elif args.case in ("c128", "df64"):
         n, batch = 1 << 20, 16
         x = torch.randn(batch, n, dtype=torch.complex128, device="cuda")
         y = torch.empty_like(x)

@@ -408,6 +408,7 @@ struct SizeClass {
     Schedule sched;
     int64_t chunk = 1;           // transforms per workspace round
     std::vector<int64_t> offs;   // element offsets (uneven plans)
+    bool off_even = true;        // every offset a multiple of 2 points
     DevBuf d_off;                // the same on the device
 };
 
@@ -637,9 +638,11 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
     }
     size_t eb = elem_bytes(p->dt);
     // transforms per workspace round: 256 MiB of complex128 (FP64-bound
-    // passes: fewer launches and wave tails), 512 MiB of complex64 (measured:
-    // L2-sized rounds cost more in launch tails than their L2 reuse saves)
-    const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)512 << 20);
+    // passes: fewer launches and wave tails), 2 GiB of complex64 (measured on
+    // n = 2^16 x 4096: rounds of 32 / 128 / 512 / 1024 / 4096 transforms take
+    // 3.10 / 1.97 / 1.57 / 1.50 / 1.44 ms -- L2-sized rounds cost more in
+    // launch tails than their L2 reuse saves)
+    const int64_t target = p->dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)2048 << 20);
     int64_t ws = 0;
     for (auto &c : p->classes) {
         if (c.sched.unblocked) {
@@ -656,6 +659,8 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
             c.chunk = c.count;
         }
         if (!c.offs.empty()) {
+            c.off_even = true;
+            for (int64_t o : c.offs) c.off_even = c.off_even && (o % 2 == 0);
             int st = dev_alloc(c.d_off, c.offs.size() * sizeof(int64_t), "offset table");
             if (st != FFT_OK) return st;
             e = cudaMemcpy(c.d_off.ptr, c.offs.data(), c.offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -1031,6 +1036,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.out = (i == S.npass - 1) ? (void *)dst : p->ws.ptr;
             a.in_off = (i == 0) ? off : nullptr;
             a.out_off = (i == S.npass - 1) ? off : nullptr;
+            a.off_even = C.off_even ? 1 : 0;
             a.count = c;
             a.log_r = d.log_r;
             a.width = d.width;

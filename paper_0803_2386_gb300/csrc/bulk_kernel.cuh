@@ -28,20 +28,49 @@ namespace moafft {
 
 constexpr uint32_t kBulkWaitPolls = 1u << 22;
 
-// bulk copies need 16-byte rows: W * 8 >= 16 for complex64
-__host__ __device__ constexpr bool bulk_ok(int logr) { return logr >= 4 && logr <= 11; }
+// column tiles need 16-byte box rows (W * 8 >= 16 for complex64); row
+// tiles are whole rows of up to 2^12 points
+__host__ __device__ constexpr bool bulk_ok(int logr, bool last) { return logr >= 4 && logr <= (last ? 12 : 11); }
+
+// row pitch of the row-tile stage: R plus a pad that keeps rows 16-byte
+// aligned and puts the W rows a half-warp reads in different banks (exact
+// for W <= 8; wider tiles keep a two-way conflict)
+template <int LOGR>
+__host__ __device__ constexpr int bulk_row_pitch()
+{
+    return (1 << LOGR) + (tile_width(LOGR) >= 8 ? 2 : 16 / tile_width(LOGR));
+}
 
 template <int LOGR, bool LAST>
 __host__ __device__ constexpr size_t bulk_stage_elems()
 {
-    return LAST ? (size_t)tile_width(LOGR) * ((1 << LOGR) + 2) : (size_t)(1 << LOGR) * tile_width(LOGR);
+    return LAST ? (size_t)tile_width(LOGR) * bulk_row_pitch<LOGR>() : (size_t)(1 << LOGR) * tile_width(LOGR);
+}
+
+// Staged output rows of a single-pass tile.  Rows of up to 2^10 points are
+// kept contiguous (pitch R + 2, 16-byte aligned) and leave by one bulk copy
+// each; longer rows, whose digit-reversed staging writes would conflict up
+// to 16-way in that layout, are kept at padded positions tpad(k) with a pitch
+// that makes the writes conflict-free and leave by coalesced 16-byte stores
+// (measured faster for 2^11 and 2^12, slower for 2^10).
+template <int LOGR>
+__host__ __device__ constexpr bool bulk_out_padded() { return LOGR >= 11; }
+template <int LOGR>
+__host__ __device__ constexpr int bulk_out_pitch()
+{
+    return bulk_out_padded<LOGR>() ? (1 << LOGR) + (1 << LOGR) / 16 + (LOGR == 11 ? 4 : 1) : (1 << LOGR) + 2;
 }
 
 template <int LOGR, bool LAST>
 __host__ __device__ constexpr size_t bulk_smem_bytes()
 {
     return 2 * bulk_stage_elems<LOGR, LAST>() * sizeof(float2) +
-           (LOGR >= 5 ? (size_t)((1 << LOGR) + (1 << LOGR) / 16) * tile_width(LOGR) * sizeof(float2) : 0) + 64;
+           (LOGR >= 5 ? (size_t)(LAST && bulk_out_pitch<LOGR>() > (1 << LOGR) + (1 << LOGR) / 16
+                                     ? bulk_out_pitch<LOGR>()
+                                     : (1 << LOGR) + (1 << LOGR) / 16) *
+                            tile_width(LOGR) * sizeof(float2)
+                      : 0) +
+           64;
 }
 
 // warp 0: start the copies of tile `cta` into stage `buf`
@@ -99,9 +128,9 @@ __device__ __forceinline__ void bulk_issue(const PassArgs &p, const CUtensorMap 
                 }
                 src = tr0 * n + a * (int64_t)R;
             } else {
-                src = (tr0 + w) * n;
+                src = p.in_off ? p.in_off[tr0 + w] : (tr0 + w) * n;
             }
-            tc::bulk_g2s(stage + (size_t)w * (R + 2), in + src, R * sizeof(float2), mbar);
+            tc::bulk_g2s(stage + (size_t)w * bulk_row_pitch<LOGR>(), in + src, R * sizeof(float2), mbar);
         }
     }
 }
@@ -127,6 +156,12 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2)
     const int tid = threadIdx.x;
     const int w = tid % W, u = tid / W;
     const long long G = gridDim.x;
+    // single-pass plans (A = 1) with a 16-byte aligned output: the rows are
+    // staged in the exchange tile and leave as whole rows
+    constexpr int kOutPitch = bulk_out_pitch<LOGR>();
+    constexpr bool kPadded = bulk_out_padded<LOGR>();
+    const bool staged = LAST && LOGR >= 5 && p.A == 1 && (((uintptr_t)p.out) & 15) == 0 &&
+                        (p.out_off == nullptr || p.off_even);
     long long t = blockIdx.x;
     if (t >= total) return;
     if (tid == 0) {
@@ -150,16 +185,53 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2)
 #pragma unroll
             for (int e = 0; e < E0; e++) {
                 const int m = e * Q0 + g * U + u;
-                v[g * E0 + e] = LAST ? st[(size_t)w * (R + 2) + m] : st[(size_t)m * W + w];
+                v[g * E0 + e] = LAST ? st[(size_t)w * bulk_row_pitch<LOGR>() + m] : st[(size_t)m * W + w];
             }
+        if (staged && !kPadded && tid == 0) tc::bulk_wait_read();  // the previous rows have left the tile
         __syncthreads();  // every thread has read this stage
         if (tid < 32 && t + 2 * G < total) {
             tc::fence_proxy_async();
             bulk_issue<LOGR, LAST>(p, &tmap, t + 2 * G, stage + buf * SE, &mbar[buf]);
         }
-        tile_finish<float, DIR, LOGR, LAST, W>(p, r, v, tile);
+        if (staged) {
+            // single-pass rows: natural-order rows staged in the exchange tile
+            tile_finish<float, DIR, LOGR, LAST, W, kOutPitch, kPadded>(p, r, v, tile);
+            const int64_t tr0 = t * W;
+            const int rows = (int)min((int64_t)W, p.count - tr0);
+            float2 *out = reinterpret_cast<float2 *>(p.out);
+            if constexpr (kPadded) {
+                // two consecutive points per thread, 16-byte coalesced stores
+                __syncthreads();
+                constexpr int T = tile_threads(LOGR);
+#pragma unroll
+                for (int it = 0; it < (W * R / 2) / T; it++) {
+                    const int f = 2 * (tid + it * T);
+                    const int row = f >> LOGR, i = f & (R - 1);
+                    if (row < rows) {
+                        const float2 a = tile[row * kOutPitch + tpad(i)];
+                        const float2 b = tile[row * kOutPitch + tpad(i + 1)];
+                        const int64_t dst = (p.out_off ? p.out_off[tr0 + row] : (tr0 + row) * p.n) + i;
+                        *reinterpret_cast<float4 *>(out + dst) = make_float4(a.x, a.y, b.x, b.y);
+                    }
+                }
+            } else {
+                // one bulk copy per row
+                tc::fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w2 = 0; w2 < rows; w2++) {
+                        const int64_t dst = p.out_off ? p.out_off[tr0 + w2] : (tr0 + w2) * p.n;
+                        tc::bulk_s2g(out + dst, tile + w2 * kOutPitch, (uint32_t)(R * sizeof(float2)));
+                    }
+                    tc::bulk_commit();
+                }
+            }
+        } else {
+            tile_finish<float, DIR, LOGR, LAST, W>(p, r, v, tile);
+        }
         __syncthreads();  // the next tile reuses the exchange tile
     }
+    if (staged && !kPadded && tid == 0) tc::bulk_wait_all();
 }
 
 }  // namespace moafft

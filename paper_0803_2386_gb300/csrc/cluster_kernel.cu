@@ -112,9 +112,6 @@ __device__ __forceinline__ void tensor_s2g_2d(const void *tmap, int x, int y, co
                  "r"(y), "r"(tc::smem_u32(smem_src))
                  : "memory");
 }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // byte offset of output point (k', row) in the staging area: boxes of 256
 // rows k' x 16 points (128 B), each in the TMA's 128-byte swizzle (the
@@ -209,7 +206,7 @@ __global__ void __launch_bounds__(Geo<C>::threads, C == 16 ? 2 : 1)
         for (int j = 0; j < 16; j++) S[(u1 + 16 * j) * kCols + (w1 ^ ((u1 & 1) << 3))] = v[j];
         // the previous transform's output boxes have left the staging area
         // before any thread passes the barrier below
-        if (tid == 0) bulk_wait_read();
+        if (tid == 0) tc::bulk_wait_read();
         cluster_arrive();
         cluster_wait();
 
@@ -247,10 +244,10 @@ __global__ void __launch_bounds__(Geo<C>::threads, C == 16 ? 2 : 1)
 #pragma unroll
             for (int h = 0; h < kCols / 16; h++)
                 tensor_s2g_2d(&tmap_out, (int)(rank * kCols) + 16 * h, (int)(t * kSide), base + h * kSide * 128);
-            bulk_commit();
+            tc::bulk_commit();
         }
     }
-    if (tid == 0) bulk_wait_all();
+    if (tid == 0) tc::bulk_wait_all();
     if (cnt > 0) cluster_wait();  // no CTA leaves while a peer may still read its buffers
 }
 

@@ -85,6 +85,7 @@ struct PassArgs {
     // `out` (stores); NULL means the dense layout tr * n
     const int64_t *in_off;
     const int64_t *out_off;
+    int off_even;  // every offset is a multiple of 2 points (16-byte rows)
     // device word set to 1 when a bounded wait inside a kernel gave up
     int *err;
     // tensor-core form: the split 32x32 DFT matrix of this direction, hi

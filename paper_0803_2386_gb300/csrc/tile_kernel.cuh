@@ -237,7 +237,11 @@ __device__ __forceinline__ void tile_load(const PassArgs &p, const TileRef &r, t
 }
 
 // 2.-4. codelets, shared-memory exchanges, weights, stores
-template <typename T, int DIR, int LOGR, bool LAST, int W>
+// STAGE > 0 (last pass of a single-pass plan, A = 1): instead of storing to
+// HBM, point k of row w is left (scaled) in shared memory at
+// tile[w * STAGE + k] (PADDED false) or tile[w * STAGE + tpad(k)] (PADDED
+// true), for the caller to store whole rows.
+template <typename T, int DIR, int LOGR, bool LAST, int W, int STAGE = 0, bool PADDED = false>
 __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r, typename cvec<T>::type *v,
                                             typename cvec<T>::type *tile)
 {
@@ -328,6 +332,19 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             revu |= digits[j] << shift;
             shift += 4;
         }
+    }
+    if constexpr (LAST && STAGE > 0) {
+        __syncthreads();  // every thread has finished with the exchange tile
+        const bool scale = p.scale != 1.0;
+        const auto sf = M::prep(p.scale);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            V x = v[j];
+            if (scale) M::scale(x, sf);
+            const int kk = revu + U * j;
+            tile[w * STAGE + (PADDED ? tpad(kk) : kk)] = x;
+        }
+        return;
     }
     if (!valid) return;
     if constexpr (!LAST) {

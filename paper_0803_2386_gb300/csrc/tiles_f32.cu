@@ -123,7 +123,10 @@ static cudaError_t launch_bulk_dir(const PassArgs &a, cudaStream_t s)
     case 8: return launch_bulk_one<DIR, 8, LAST>(a, s);
     case 9: return launch_bulk_one<DIR, 9, LAST>(a, s);
     case 10: return launch_bulk_one<DIR, 10, LAST>(a, s);
-    default: return launch_bulk_one<DIR, 11, LAST>(a, s);
+    case 11: return launch_bulk_one<DIR, 11, LAST>(a, s);
+    default:
+        if constexpr (LAST) return launch_bulk_one<DIR, 12, true>(a, s);
+        return cudaErrorNotSupported;
     }
 }
 
@@ -149,7 +152,9 @@ cudaError_t launch_tile_f32(const PassArgs &a, int dir, cudaStream_t s)
     // column tiles by 2-D tensor-map boxes; dense, 16-byte aligned input
     static const bool bulk = getenv("MOAFFT_NO_BULK") == nullptr;
     static const bool cols = getenv("MOAFFT_NO_TMA_COLUMNS") == nullptr;
-    if (bulk && (a.is_last || cols) && bulk_ok(a.log_r) && a.in_off == nullptr && ((uintptr_t)a.in % 16) == 0) {
+    // ragged (uneven) inputs: single-pass rows whose offsets keep 16-byte rows
+    const bool dense_in = a.in_off == nullptr || (a.is_last && a.A == 1 && a.off_even);
+    if (bulk && (a.is_last || cols) && bulk_ok(a.log_r, a.is_last) && dense_in && ((uintptr_t)a.in % 16) == 0) {
         cudaError_t e;
         if (dir < 0) e = a.is_last ? launch_bulk_dir<-1, true>(a, s) : launch_bulk_dir<-1, false>(a, s);
         else e = a.is_last ? launch_bulk_dir<1, true>(a, s) : launch_bulk_dir<1, false>(a, s);
