@@ -307,7 +307,7 @@ def run_moafft(args):
     avg_ms = ms_tot / max(cnt, 1)
     flops_launch = 5.0 * chunk * n * log_r
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
-    kname = f"pass_kernel<double> pass {dom} (log2 R = {log_r})"
+    kname = f"tile_kernel<double> pass {dom} (log2 R = {log_r})"
     wkey = f"c128 n=2^{args.log2n}"
     traffic = recorded_traffic(f"pass{dom}", wkey)
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
