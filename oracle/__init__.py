@@ -41,6 +41,7 @@ _OPS = {"forward": FORWARD, "inverse": INVERSE,
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_intp = ctypes.POINTER(ctypes.c_int)
 
 
 def lib():
@@ -72,6 +73,10 @@ def lib():
                                             ctypes.c_int, ctypes.c_int]),
             "oracle_fft_many": (ctypes.c_int, [_f64p, _f64p, ctypes.c_int64, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_int64, ctypes.c_int]),
+            "moa_dm_perm": (ctypes.c_int, [ctypes.c_int, _intp, ctypes.c_int, _i64p]),
+            "moa_dm_gate_c128": (ctypes.c_int, [_f64p, ctypes.c_int, _intp, ctypes.c_int, _f64p]),
+            "moa_dm_gate_block_c128": (ctypes.c_int, [_f64p, ctypes.c_int, _intp, ctypes.c_int, _f64p,
+                                                      ctypes.c_int64, ctypes.c_int64, _f64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -237,3 +242,46 @@ def fft(x, op: str = "forward", c: int = 1024, threads: int = 1) -> np.ndarray:
 
 def library_path() -> str:
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboracle.so")
+
+
+# ------------------------------------------------- density-matrix gating --
+
+def _qubits(qubits) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(qubits, dtype=np.int32))
+
+
+def dm_perm(n: int, qubits) -> np.ndarray:
+    """Transpose vector t (length 2n) that moves the gated qubits' axes of the
+    2^(2n) hyper-cube behind the others in both halves (Ch. "Density Matrix
+    Operations", Sec. "The Algorithm")."""
+    qb = _qubits(qubits)
+    t = np.zeros(2 * n, dtype=np.int64)
+    _check(lib().moa_dm_perm(n, qb.ctypes.data_as(_intp), len(qb), _ip(t)), "moa_dm_perm")
+    return t
+
+
+def dm_gate(rho, qubits, u) -> np.ndarray:
+    """rho' = G rho G^H, G = u on the gated qubits (the highest gated qubit is
+    the most significant bit of u's index), computed block by block in the
+    transposed view.  rho: 2^n x 2^n complex; returns a new array."""
+    r = _c128(rho).copy()
+    N = r.shape[0]
+    n = int(N).bit_length() - 1
+    qb = _qubits(qubits)
+    uu = _c128(u)
+    _check(lib().moa_dm_gate_c128(_fp(r), n, qb.ctypes.data_as(_intp), len(qb), _fp(uu)), "moa_dm_gate_c128")
+    return r
+
+
+def dm_gate_block(rho, qubits, u, I: int, J: int) -> np.ndarray:
+    """Block (I, J) of the transposed view after the gate: U B_IJ U^H."""
+    r = _c128(rho)
+    N = r.shape[0]
+    n = int(N).bit_length() - 1
+    qb = _qubits(qubits)
+    m = 1 << len(qb)
+    out = np.zeros((m, m), dtype=np.complex128)
+    _check(lib().moa_dm_gate_block_c128(_fp(r), n, qb.ctypes.data_as(_intp), len(qb), _fp(_c128(u)), I, J,
+                                        _fp(out)), "moa_dm_gate_block_c128")
+    return out
+

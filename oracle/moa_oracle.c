@@ -20,6 +20,11 @@
  *     gammadef), rotate phi, the hyper-cube transpose with a permutation
  *     vector, t_j (Eq. tvec), reshape-transpose and final transpose on index
  *     arrays, and the transformed weight vector xi.
+ *   - density-matrix gating (Ch. "Density Matrix Operations for a Quantum
+ *     Computer"): the transpose vector that brings the gated qubits of the
+ *     2^(2n) hyper-cube together, the element addresses of the transposed
+ *     view through gamma (Eq. generic), and rho <- G rho G^H applied block by
+ *     block in that view.
  *
  * Arithmetic: IEEE binary64, round-to-nearest, compiled with
  * -ffp-contract=off so that no multiply-add is fused.  Every FFT routine
@@ -548,5 +553,134 @@ int oracle_fft_many(const double *in, double *out, int64_t n, int64_t batch, int
     for (int k = 0; k < threads; k++)
         if (jobs[k].status != OR_OK)
             return jobs[k].status;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Density-matrix gating by hyper-cube transpose (Ch. "Density Matrix       */
+/* Operations for a Quantum Computer")                                      */
+/* ------------------------------------------------------------------------ */
+
+/* The transpose vector t of Sec. "The Algorithm": in each half of the 2n
+ * hyper-cube axes (row bits, then column bits, most significant first), the
+ * axes of the gated qubits are moved behind the others, both groups keeping
+ * their order.  Axis p of a half is bit n-1-p.  Reading: t[j] names the
+ * axis of D_h that becomes axis j of the transposed array (the swap table
+ * of the worked example; under the other reading the printed xabx vector
+ * would not bring bits a and b together). */
+int moa_dm_perm(int n, const int *qubits, int q, int64_t *t)
+{
+    if (n < 1 || n > 30 || q < 1 || q > n || !qubits || !t)
+        return OR_ERR_ARG;
+    int gated[64] = {0};
+    for (int k = 0; k < q; k++) {
+        if (qubits[k] < 0 || qubits[k] >= n || gated[n - 1 - qubits[k]])
+            return OR_ERR_ARG;
+        gated[n - 1 - qubits[k]] = 1; /* axis of bit qubits[k] */
+    }
+    int pos = 0;
+    for (int p = 0; p < n; p++)
+        if (!gated[p])
+            t[pos++] = p;
+    for (int p = 0; p < n; p++)
+        if (gated[p])
+            t[pos++] = p;
+    for (int j = 0; j < n; j++)
+        t[n + j] = t[j] + n;
+    return OR_OK;
+}
+
+/* Address of element (row r', column c') of the transposed array t tr D_h,
+ * through the normal form of Eq. generic: gamma(i[t]; s) with s = <2 ... 2>
+ * and i = the binary digits of r' then c' -- here the transposed index is
+ * applied as i_old[t[j]] = i[j]. */
+static int64_t dm_address(int n, const int64_t *t, int64_t rp, int64_t cp)
+{
+    int64_t iv[64], iold[64], shape[64];
+    for (int j = 0; j < n; j++) {
+        iv[j] = (rp >> (n - 1 - j)) & 1;
+        iv[n + j] = (cp >> (n - 1 - j)) & 1;
+    }
+    for (int j = 0; j < 2 * n; j++) {
+        iold[t[j]] = iv[j];
+        shape[j] = 2;
+    }
+    return moa_gamma_row(2 * n, shape, iold);
+}
+
+/* out (2^q x 2^q) = U B U^H for block (I, J) of the transposed array: B is
+ * rows I 2^q + g, columns J 2^q + h (g, h < 2^q) -- the gate acts on the
+ * gated qubits, the highest gated qubit being the most significant bit of
+ * g and h. */
+static int dm_block(const cplx *rho, int n, const int64_t *t, int q, const cplx *u, int64_t I, int64_t J,
+                    cplx *out)
+{
+    const int64_t m = (int64_t)1 << q;
+    cplx B[64], T[64];
+    for (int64_t g = 0; g < m; g++)
+        for (int64_t h = 0; h < m; h++)
+            B[g * m + h] = rho[dm_address(n, t, I * m + g, J * m + h)];
+    for (int64_t a = 0; a < m; a++) /* T = U B */
+        for (int64_t h = 0; h < m; h++) {
+            double re = 0.0, im = 0.0;
+            for (int64_t c = 0; c < m; c++) {
+                const cplx x = u[a * m + c], y = B[c * m + h];
+                re += x.re * y.re - x.im * y.im;
+                im += x.re * y.im + x.im * y.re;
+            }
+            T[a * m + h].re = re;
+            T[a * m + h].im = im;
+        }
+    for (int64_t a = 0; a < m; a++) /* out = T U^H */
+        for (int64_t b = 0; b < m; b++) {
+            double re = 0.0, im = 0.0;
+            for (int64_t c = 0; c < m; c++) {
+                const cplx x = T[a * m + c], y = u[b * m + c]; /* U^H[c][b] = conj(U[b][c]) */
+                re += x.re * y.re + x.im * y.im;
+                im += x.im * y.re - x.re * y.im;
+            }
+            out[a * m + b].re = re;
+            out[a * m + b].im = im;
+        }
+    return OR_OK;
+}
+
+/* One block only (for sampled checks of large matrices). */
+int moa_dm_gate_block_c128(const double *rho, int n, const int *qubits, int q, const double *u, int64_t I,
+                           int64_t J, double *out)
+{
+    int64_t t[64];
+    int st = moa_dm_perm(n, qubits, q, t);
+    if (st != OR_OK)
+        return st;
+    if (q > 3)
+        return OR_ERR_ARG;
+    const int64_t nb = (int64_t)1 << (n - q);
+    if (I < 0 || J < 0 || I >= nb || J >= nb)
+        return OR_ERR_ARG;
+    return dm_block((const cplx *)rho, n, t, q, (const cplx *)u, I, J, (cplx *)out);
+}
+
+/* rho <- G rho G^H in place, G = U on the gated qubits (identity on the
+ * others): every 2^q x 2^q block of the transposed array becomes U B U^H
+ * (in that view G is block diagonal, diag(U, ..., U)). */
+int moa_dm_gate_c128(double *rho, int n, const int *qubits, int q, const double *u)
+{
+    int64_t t[64];
+    int st = moa_dm_perm(n, qubits, q, t);
+    if (st != OR_OK)
+        return st;
+    if (q > 3)
+        return OR_ERR_ARG;
+    const int64_t m = (int64_t)1 << q, nb = (int64_t)1 << (n - q);
+    cplx *R = (cplx *)rho;
+    cplx out[64];
+    for (int64_t I = 0; I < nb; I++)
+        for (int64_t J = 0; J < nb; J++) {
+            dm_block(R, n, t, q, (const cplx *)u, I, J, out);
+            for (int64_t g = 0; g < m; g++)
+                for (int64_t h = 0; h < m; h++)
+                    R[dm_address(n, t, I * m + g, J * m + h)] = out[g * m + h];
+        }
     return OR_OK;
 }
