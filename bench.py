@@ -611,6 +611,27 @@ def extra_configs(M, torch, dev, stream):
            "gbs": round(4 * n * batch * 8 / (ms * 1e-3) / 1e9, 1)})
     pd.close()
 
+    # density-matrix gating by hyper-cube transpose: 14 qubits (2^28 elements,
+    # larger than L2), in place; algorithmic bytes = one read + one write;
+    # flops = the two 2^q x 2^q complex products per block
+    nq = 14
+    for f64 in (True, False):
+        tdt = torch.complex128 if f64 else torch.complex64
+        eb = 16 if f64 else 8
+        rho = torch.randn(1 << nq, 1 << nq, dtype=tdt, device=dev)
+        for qubits in ([0], [13], [1, 12]):
+            q = len(qubits)
+            u = np.linalg.qr(np.random.default_rng(q).standard_normal((1 << q, 1 << q)))[0].astype(np.complex128)
+            ms = _time(torch, stream, lambda: M.dm_gate(rho, qubits, u, stream), 10)
+            elems = float(1 << (2 * nq))
+            gbs = 2 * elems * eb / (ms * 1e-3) / 1e9
+            flops = elems / (1 << (2 * q)) * 2 * (1 << (3 * q)) * 8
+            _emit({"config": f"density-matrix gate, {nq} qubits, qubits {qubits}, {'c128' if f64 else 'c64'}",
+                   "ms": round(ms, 3), "gbs": round(gbs, 1),
+                   "hbm_frac_of_measured": round(gbs / hbm, 4) if hbm else None,
+                   "gflops": round(flops / (ms * 1e-3) / 1e9, 1)})
+        del rho
+
 
 def max_over_ranks(value: float, dist, device) -> float:
     """The slowest rank's time (the job's time)."""

@@ -221,6 +221,38 @@ int fft_set_allocator(fft_alloc_fn alloc, fft_free_fn release, void *ctx);
  * time) and Table 4 (the radix sweep). */
 int fft_tune_candidates(int64_t n, fft_dtype dt, fft_form form, char *buf, int64_t len);
 
+/* ---- density-matrix gating by hyper-cube transpose ----------------------
+ * (Ch. "Density Matrix Operations for a Quantum Computer")
+ *
+ * The 2^n x 2^n density matrix rho is viewed as a hyper-cube of 2n axes of
+ * length 2 (row bits, then column bits, most significant first).  A
+ * transpose vector t moves the axes of the gated qubits behind the others in
+ * both halves; in that view a gate on those qubits is block diagonal, and
+ * rho <- G rho G^H becomes B <- U B U^H on every 2^q x 2^q block.  The view
+ * is never built: elements are addressed through the normal form
+ * @D + gamma(i[t]; s) (Eq. generic). */
+
+/* Apply rho <- G rho G^H in place, G = u on the gated qubits and the
+ * identity on the others.
+ *   rho      device pointer, 2^n_qubits x 2^n_qubits complex (interleaved
+ *            re, im; row-major), dtype dt (FFT_C64 or FFT_C128), aligned to
+ *            its element size; 1 <= n_qubits <= 15.
+ *   qubits   host array of q distinct qubit numbers, bit positions counted
+ *            from the right (0 <= qubit < n_qubits); their order does not
+ *            matter.  q = 1 or 2.
+ *   u        host pointer to the 2^q x 2^q gate, row-major, same dtype; bit
+ *            q-1 of its row/column index is the highest gated qubit.
+ * Asynchronous on cuda_stream (NULL: the default stream).  Errors:
+ * FFT_ERR_ARG (NULL pointers, host or misaligned rho, bad n or qubits),
+ * FFT_ERR_DTYPE, FFT_ERR_UNSUPPORTED (q > 2, n > 15), FFT_ERR_CUDA. */
+int dm_gate(void *rho, int n_qubits, const int *qubits, int q, const void *u, fft_dtype dt,
+            void *cuda_stream);
+
+/* The transpose vector t of the gating above, 2 n_qubits entries written to
+ * t_out: t[j] is the hyper-cube axis that becomes axis j of the view (for
+ * n = 4, qubits {0, 2}: 0 2 1 3 4 6 5 7).  Host logic only. */
+int dm_transpose_vector(int n_qubits, const int *qubits, int q, int *t_out);
+
 /* Library version as 10000*major + 100*minor + patch. */
 int fft_version(void);
 

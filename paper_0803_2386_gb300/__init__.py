@@ -41,7 +41,8 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
 # every symbol include/moafft.h declares
 EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_exec", "fft_exec_adjoint",
            "fft_exec_host", "fft_exec_noalloc", "fft_plan_check", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
-           "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_tune_candidates", "fft_version"]
+           "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_tune_candidates", "fft_version",
+           "dm_gate", "dm_transpose_vector"]
 
 _LIB = None
 
@@ -92,6 +93,8 @@ def lib():
             "fft_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
             "fft_tune_candidates": (i32, [i64, i32, i32, ctypes.c_char_p, i64]),
             "fft_version": (i32, []),
+            "dm_gate": (i32, [vp, i32, ctypes.POINTER(i32), i32, vp, i32, vp]),
+            "dm_transpose_vector": (i32, [i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -185,6 +188,34 @@ def fft_exec_noalloc(inp, out, n: int, batch: int, dtype: int, direction: int = 
     scratch; see include/moafft.h for the limits)."""
     _check(lib().fft_exec_noalloc(_ptr(inp), _ptr(out), n, batch, dtype, direction,
                                   _stream(stream, inp, out)))
+
+
+def _int_array(values):
+    arr = (ctypes.c_int * max(1, len(values)))(*[int(v) for v in values])
+    return arr
+
+
+def dm_transpose_vector(n_qubits: int, qubits) -> list:
+    """The hyper-cube transpose vector that gathers the gated qubits (host
+    logic; Ch. "Density Matrix Operations", Sec. "The Algorithm")."""
+    qb = _int_array(qubits)
+    out = (ctypes.c_int * (2 * max(1, n_qubits)))()
+    _check(lib().dm_transpose_vector(n_qubits, qb, len(qubits), out))
+    return list(out)[:2 * n_qubits]
+
+
+def dm_gate(rho, qubits, u, stream=None):
+    """rho <- G rho G^H in place on the GPU, G = u on the gated qubits.
+    rho: square complex64/complex128 CUDA tensor of side 2^n; u: 2^q x 2^q
+    (numpy or tensor on any device), converted to rho's dtype."""
+    import numpy as np
+    side = int(rho.shape[-1])
+    n = side.bit_length() - 1
+    dt = FFT_C128 if str(rho.dtype).endswith("complex128") else FFT_C64
+    uu = np.ascontiguousarray(np.asarray(u.cpu() if hasattr(u, "cpu") else u,
+                                         dtype=np.complex128 if dt == FFT_C128 else np.complex64))
+    qb = _int_array(qubits)
+    _check(lib().dm_gate(_ptr(rho), n, qb, len(qubits), uu.ctypes.data, dt, _stream(stream, rho)))
 
 
 def fft_plan_check(plan: int):

@@ -1456,4 +1456,50 @@ extern "C" int64_t fft_plan_launches(fft_plan_t p) { return p ? launches_per_exe
 
 extern "C" int64_t fft_plan_workspace_bytes(fft_plan_t p) { return p ? p->ws_bytes : 0; }
 
+// ------------------------------------------------ density-matrix gating --
+
+static int dm_check(int n, const int *qubits, int q)
+{
+    if (!qubits) return fail(FFT_ERR_ARG, "qubits is NULL");
+    if (n < 1 || n > 30) return fail(FFT_ERR_ARG, "n_qubits = %d outside 1..30", n);
+    if (q < 1 || q > n) return fail(FFT_ERR_ARG, "q = %d outside 1..n_qubits", q);
+    for (int k = 0; k < q; k++) {
+        if (qubits[k] < 0 || qubits[k] >= n) return fail(FFT_ERR_ARG, "qubit %d outside 0..%d", qubits[k], n - 1);
+        for (int j = 0; j < k; j++)
+            if (qubits[j] == qubits[k]) return fail(FFT_ERR_ARG, "qubit %d listed twice", qubits[k]);
+    }
+    return FFT_OK;
+}
+
+extern "C" int dm_transpose_vector(int n, const int *qubits, int q, int *t_out)
+{
+    int st = dm_check(n, qubits, q);
+    if (st != FFT_OK) return st;
+    if (!t_out) return fail(FFT_ERR_ARG, "t_out is NULL");
+    // axis p of a half carries bit n-1-p; gated axes go behind the others
+    bool gated[64] = {false};
+    for (int k = 0; k < q; k++) gated[n - 1 - qubits[k]] = true;
+    int pos = 0;
+    for (int pass = 0; pass < 2; pass++)
+        for (int p = 0; p < n; p++)
+            if (gated[p] == (pass == 1)) t_out[pos++] = p;
+    for (int j = 0; j < n; j++) t_out[n + j] = t_out[j] + n;
+    return FFT_OK;
+}
+
+extern "C" int dm_gate(void *rho, int n, const int *qubits, int q, const void *u, fft_dtype dt, void *cuda_stream)
+{
+    if (dt != FFT_C64 && dt != FFT_C128) return fail(FFT_ERR_DTYPE, "unknown dtype %d", (int)dt);
+    int st = dm_check(n, qubits, q);
+    if (st != FFT_OK) return st;
+    if (!u) return fail(FFT_ERR_ARG, "u is NULL");
+    if (q > 2) return fail(FFT_ERR_UNSUPPORTED, "gates on %d qubits: the kernel takes 1 or 2", q);
+    if (n > 15) return fail(FFT_ERR_UNSUPPORTED, "n_qubits = %d: the kernel takes up to 15", n);
+    st = check_device_ptr(rho, elem_bytes(dt), "rho");
+    if (st != FFT_OK) return st;
+    cudaError_t e = launch_dm_gate(rho, n, qubits, q, u, dt == FFT_C128, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail_cuda(e, "density-matrix gate launch");
+    return FFT_OK;
+}
+
 extern "C" int fft_version(void) { return 100; }

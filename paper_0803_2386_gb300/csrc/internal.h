@@ -129,6 +129,9 @@ int cluster_ctas();        // CTAs per cluster (16, or 8 when 16 does not fit)
 cudaError_t launch_cluster_f32(const void *in, void *out, int64_t count, const void *tw, double scale, int *err,
                                int dir, cudaStream_t s);
 
+// density-matrix gating (dm_gate.cu): q = 1 or 2, qubits checked by the caller
+cudaError_t launch_dm_gate(void *rho, int n, const int *qubits, int q, const void *u, bool f64, cudaStream_t s);
+
 // kernel launchers (kernels_f32.cu / kernels_f64.cu)
 cudaError_t launch_pass_f32(const PassArgs &a, int dir, cudaStream_t s);
 cudaError_t launch_pass_f64(const PassArgs &a, int dir, cudaStream_t s);

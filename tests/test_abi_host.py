@@ -24,7 +24,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", h)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(fft_[a-z_0-9]+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b((?:fft|dm)_[a-z_0-9]+)\s*\(",
                              text, flags=re.M):
             names.append(m.group(1))
     return sorted(set(names))
@@ -148,3 +148,23 @@ def test_cluster_schedule_describes_two_groups():
         assert e.value.status == M.FFT_ERR_UNSUPPORTED
     assert "cluster" in M.fft_tune_candidates(1 << 16, M.FFT_C64)
     assert "cluster" not in M.fft_tune_candidates(1 << 16, M.FFT_C128)
+
+
+def test_dm_transpose_vector_matches_the_paper_and_the_oracle():
+    """Host-side transpose vector of the gating entry point: the printed
+    worked examples, and the oracle's construction for other qubit sets."""
+    import oracle as O
+    assert M.dm_transpose_vector(4, [0, 2]) == [0, 2, 1, 3, 4, 6, 5, 7]
+    assert M.dm_transpose_vector(4, [2, 1]) == [0, 3, 1, 2, 4, 7, 5, 6]
+    for n, qb in [(1, [0]), (5, [4]), (6, [0, 5]), (7, [3, 1, 6])]:
+        assert M.dm_transpose_vector(n, qb) == list(O.dm_perm(n, qb))
+
+
+def test_dm_gate_argument_errors():
+    L = M.lib()
+    for n, qb in [(4, [4]), (4, [1, 1]), (0, [0]), (3, [-1])]:
+        with pytest.raises(M.MoaFFTError) as e:
+            M.dm_transpose_vector(n, qb)
+        assert e.value.status == M.FFT_ERR_ARG
+    assert L.dm_gate(None, 4, None, 1, None, M.FFT_C64, None) == M.FFT_ERR_ARG
+
