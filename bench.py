@@ -618,7 +618,8 @@ def extra_configs(M, torch, dev, stream):
     for f64 in (True, False):
         tdt = torch.complex128 if f64 else torch.complex64
         eb = 16 if f64 else 8
-        rho = torch.randn(1 << nq, 1 << nq, dtype=tdt, device=dev)
+        gen = torch.Generator(device=dev).manual_seed(14)
+        rho = torch.randn(1 << nq, 1 << nq, dtype=tdt, device=dev, generator=gen)
         for qubits in ([0], [13], [1, 12]):
             q = len(qubits)
             u = np.linalg.qr(np.random.default_rng(q).standard_normal((1 << q, 1 << q)))[0].astype(np.complex128)
