@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64"],
+    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -611,6 +611,27 @@ def extra_configs(M, torch, dev, stream):
            "gbs": round(4 * n * batch * 8 / (ms * 1e-3) / 1e9, 1)})
     pd.close()
 
+    # radix sweep at n = 2^24 (the paper's Table 4 sweeps the radix of
+    # fftpsiradn at 2^24): three passes of 2^8 through the generic tile kernel
+    # (width 8 keeps every variant on the same kernel), register digits of
+    # 2, 4, 8 and 16 points; the default schedule beside them
+    for f64, batch in ((False, 8), (True, 4)):
+        n = 1 << 24
+        tdt = torch.complex128 if f64 else torch.complex64
+        gen = torch.Generator(device=dev).manual_seed(24)
+        x = torch.randn(batch, n, dtype=tdt, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        row = {"config": f"radix sweep, {'c128' if f64 else 'c64'} n=2^24 batch {batch} forward"}
+        for k in (1, 2, 3, 4, None):
+            sched = None if k is None else f"8@8/{k},8@8/{k},8@8/{k}"
+            p = M.Plan(n, batch, M.FFT_C128 if f64 else M.FFT_C64, M.FFT_FORWARD, M.FFT_FORM_PLAIN, sched)
+            ms = _time(torch, stream, lambda: p.exec(x, y, stream), 3)
+            key = "default_ms" if k is None else f"radix{1 << k}_ms"
+            row[key] = round(ms, 3)
+            p.close()
+        _emit(row)
+        del x, y
+
     # density-matrix gating by hyper-cube transpose: 14 qubits (2^28 elements,
     # larger than L2), in place; algorithmic bytes = one read + one write;
     # flops = the two 2^q x 2^q complex products per block
@@ -650,8 +671,13 @@ def run_case(args):
     import paper_0803_2386_gb300 as M
     form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
             "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN,
-            "c64_rows": M.FFT_FORM_PLAIN}[args.case]
-    if args.case == "c64_rows":  # single-pass transforms (row tiles only)
+            "c64_rows": M.FFT_FORM_PLAIN, "c1": M.FFT_FORM_PLAIN}[args.case]
+    if args.case == "c1":  # one complex128 transform of 2^10 points (latency)
+        n, batch = 1 << 10, 1
+        x = torch.randn(batch, n, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD, form)
+    elif args.case == "c64_rows":  # single-pass transforms (row tiles only)
         n, batch = 1 << 10, 1 << 16
         x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
         y = torch.empty_like(x)

@@ -125,16 +125,18 @@ static int tile_budget(fft_dtype dt) { return dt == FFT_C128 ? 4096 : 8192; }
 static int max_tile_log(fft_dtype dt) { return dt == FFT_C128 ? 11 : 11; }
 static size_t elem_bytes(fft_dtype dt) { return dt == FFT_C128 ? 16 : 8; }
 
+// register digits of at most max_digit bits, the remainder first (the
+// paper's general radix, fftpsiradn, as a dimension of the schedule)
 static void split_subpasses(PassDesc &p)
 {
-    int r = p.log_r;
+    const int r = p.log_r, d = p.max_digit;
     p.nsub = 0;
-    if (r % 4) p.sub_log[p.nsub++] = r % 4;
-    for (int k = 0; k < r / 4; k++) p.sub_log[p.nsub++] = 4;
+    if (r % d) p.sub_log[p.nsub++] = r % d;
+    for (int k = 0; k < r / d; k++) p.sub_log[p.nsub++] = d;
 }
 
 // Fill in A, B and the tile widths once the radices are known.
-static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
+static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width, const int *req_digit = nullptr)
 {
     int64_t A = 1;
     int used = 0;
@@ -163,6 +165,7 @@ static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width)
             return fail(FFT_ERR_ARG, "tile of %lld x %lld elements exceeds shared memory", (long long)R,
                         (long long)w);
         p.width = (int)w;
+        p.max_digit = (req_digit && req_digit[i] > 0) ? req_digit[i] : 4;
         split_subpasses(p);
         p.tw_m = R * p.B;
         p.tw_lo_bits = 0;
@@ -198,13 +201,15 @@ static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
     return finish_schedule(s, dt, nullptr);
 }
 
-// "r0[@w0],r1[@w1],..."
+// "r0[@w0][/k0],r1[@w1][/k1],...": radix 2^r per pass, tile width w, register
+// digits of at most 2^k points (k = 1..4; default 4)
 static int parse_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text)
 {
     s = Schedule();
     s.n = n;
     s.t = exact_log2(n);
     int widths[kMaxPasses] = {0};
+    int digits[kMaxPasses] = {0};
     const char *p = text;
     int np = 0;
     while (*p) {
@@ -220,6 +225,12 @@ static int parse_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
             widths[np] = (int)w;
             p = end;
         }
+        if (*p == '/') {
+            long k = strtol(p + 1, &end, 10);
+            if (end == p + 1 || k < 1 || k > 4) return fail(FFT_ERR_ARG, "schedule '%s': bad register digit", text);
+            digits[np] = (int)k;
+            p = end;
+        }
         np++;
         if (*p == ',') {
             p++;
@@ -230,7 +241,7 @@ static int parse_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
     }
     if (np == 0) return fail(FFT_ERR_ARG, "schedule '%s' is empty", text);
     s.npass = np;
-    return finish_schedule(s, dt, widths);
+    return finish_schedule(s, dt, widths, digits);
 }
 
 // Schedule text: "" / "auto" (heuristic) or a pass list, optionally followed
@@ -322,6 +333,15 @@ static std::vector<std::string> tune_candidates(int64_t n, fft_dtype dt)
                 out.push_back(std::to_string(r0) + "," + std::to_string(r1) + "," + std::to_string(r2));
         }
     // workspace-round variants of the default-like splits
+    // register-radix variants of the balanced two-pass split (radix-2, -4 and
+    // -8 codelets instead of radix-16)
+    if (t >= 8 && t <= 24) {
+        const int r0 = (t + 1) / 2, r1 = t - r0;
+        if (r1 >= 4 && r0 <= 12)
+            for (int k = 1; k <= 3; k++)
+                out.push_back(std::to_string(r0) + "/" + std::to_string(k) + "," + std::to_string(r1) + "/" +
+                              std::to_string(k));
+    }
     std::vector<std::string> with_chunks;
     for (const auto &c : out) {
         with_chunks.push_back(c);
@@ -732,7 +752,7 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
             const PassDesc &d = c.sched.pass[i];
             const int64_t W = std::min(32, std::max(1, 4096 >> d.log_r));
             const bool last = i == c.sched.npass - 1;
-            ok = d.log_r >= 4 && d.log_r <= 12 && d.width == W &&
+            ok = d.log_r >= 4 && d.log_r <= 12 && d.width == W && d.max_digit == 4 &&
                  (last ? (d.A == 1 || (d.A >= W && d.A % W == 0)) : (d.B >= W && d.B % W == 0));
         }
         if (!ok) st = fail(FFT_ERR_UNSUPPORTED, "the double-float form needs passes of 2^4..2^12 points (n >= 16)");
@@ -771,7 +791,7 @@ static int try_persist(fft_plan_s *p)
         if (c.sched.npass > 2) return FFT_OK;
         for (int i = 0; i < c.sched.npass; i++) {
             PassDesc &d = c.sched.pass[i];
-            if (d.log_r < 4 || d.log_r > 12) return FFT_OK;
+            if (d.log_r < 4 || d.log_r > 12 || d.max_digit != 4) return FFT_OK;
             const int64_t W = persist_width_host(d.log_r);
             const bool last = i == c.sched.npass - 1;
             if (!last && (d.B < W || d.B % W)) return FFT_OK;

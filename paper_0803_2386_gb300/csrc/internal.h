@@ -10,7 +10,7 @@
 namespace moafft {
 
 constexpr int kMaxPasses = 8;  // log2 n <= 40 with tiles of >= 2^5
-constexpr int kMaxSub = 4;     // register sub-passes per tile (4 x radix-16)
+constexpr int kMaxSub = 13;    // register sub-passes per tile (13 x radix-2 at most)
 
 // One HBM pass of the dimension-lifted signal.  The transform of length n
 // is viewed as an A x R x B array (n = A*R*B); the pass performs, for every
@@ -26,6 +26,7 @@ struct PassDesc {
     int width = 1;               // columns (rows in the last pass) per CTA
     int nsub = 0;                // register-level sub-passes inside the tile
     int sub_log[kMaxSub] = {0};  // log2 radix of each sub-pass, top digit first
+    int max_digit = 4;           // largest register digit (log2): 4 = radix-16 codelets
     int64_t A = 1, B = 1;        // n = A * R * B
     int tw_lo_bits = 0;          // mode 0: 0 = direct table, else two-level
     int tw_mode = 0;             // pass-weight table layout (PassArgs::tw_mode)

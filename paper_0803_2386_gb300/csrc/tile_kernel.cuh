@@ -117,6 +117,9 @@ __device__ __forceinline__ typename cvec<T>::type pass_weight_at(const PassArgs 
 inline bool tile_covers(const PassArgs &a)
 {
     if (a.log_r < 4 || a.log_r > 12) return false;
+    // the compile-time kernels split the tile into radix-16 digits after a
+    // first digit of log_r mod 4 bits; other splits run in pass_kernel
+    if (a.nsub != (a.log_r + 3) / 4 || a.sub_log[0] != (a.log_r % 4 ? a.log_r % 4 : 4)) return false;
     const int W = tile_width(a.log_r);
     if (a.width != W) return false;
     if (!a.is_last) return a.B >= W && a.B % W == 0;
@@ -265,14 +268,18 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     const int64_t sbase = r.sbase, b0 = r.b0, tr = r.tr, vrow = r.vrow;
     const bool valid = r.valid;
     (void)tr;
-    // ---- 2. first-digit codelets
+    // ---- 2. first-digit codelets (threads of rows / columns beyond the
+    // batch skip the arithmetic but still meet every barrier: all threads of
+    // a row or column share its validity, so the exchanges stay consistent)
+    if (valid) {
 #pragma unroll
-    for (int g = 0; g < G0; g++) {
-        dft_codelet<DIR, L0>(&v[g * E0]);
-        if constexpr (NS > 1) {
-            const int mq = g * U + u;
+        for (int g = 0; g < G0; g++) {
+            dft_codelet<DIR, L0>(&v[g * E0]);
+            if constexpr (NS > 1) {
+                const int mq = g * U + u;
 #pragma unroll
-            for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twt + mq * k));
+                for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twt + mq * k));
+            }
         }
     }
 
@@ -294,9 +301,9 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             const int pos0 = pre * S + mq;
 #pragma unroll
             for (int e = 0; e < 16; e++) v[e] = tile[tpad(pos0 + e * Q) * W + w];
-            dft_codelet<DIR, 4>(v);
+            if (valid) dft_codelet<DIR, 4>(v);
             if (j < NS - 1) {
-                if (mq != 0) {
+                if (valid && mq != 0) {
                     const int step = R / S;
 #pragma unroll
                     for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twt + mq * k * step));

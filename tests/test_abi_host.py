@@ -69,7 +69,7 @@ def test_plan_rejects_bad_batch_dtype_dir_form():
 
 
 def test_bad_schedules():
-    for text in ["3,3", "x", "5,5,", "5@3,5", "10@0", "4,4,4,4,4,4,4,4,4"]:
+    for text in ["3,3", "x", "5,5,", "5@3,5", "10@0", "4,4,4,4,4,4,4,4,4", "5/5,5", "5/0,5", "5/,5"]:
         with pytest.raises(M.MoaFFTError) as e:
             M.fft_describe_schedule(1 << 10, M.FFT_C128, M.FFT_FORM_PLAIN, text)
         assert e.value.status == M.FFT_ERR_ARG, text
@@ -167,4 +167,17 @@ def test_dm_gate_argument_errors():
             M.dm_transpose_vector(n, qb)
         assert e.value.status == M.FFT_ERR_ARG
     assert L.dm_gate(None, 4, None, 1, None, M.FFT_C64, None) == M.FFT_ERR_ARG
+
+
+def test_register_digit_schedules():
+    """'/k' limits the register digits of a pass to 2^k points (the general
+    radix of fftpsiradn as a schedule dimension); the default split is a
+    first digit of log_r mod 4 bits, then radix-16 digits."""
+    s = json.loads(M.fft_describe_schedule(1 << 16, M.FFT_C64, M.FFT_FORM_PLAIN, "10/2,6/3"))
+    assert [p["sub_log"] for p in s["passes"]] == [[2, 2, 2, 2, 2], [3, 3]]
+    s = json.loads(M.fft_describe_schedule(1 << 16, M.FFT_C64, M.FFT_FORM_PLAIN, "10,6"))
+    assert [p["sub_log"] for p in s["passes"]] == [[2, 4, 4], [2, 4]]
+    s = json.loads(M.fft_describe_schedule(1 << 13, M.FFT_C64, M.FFT_FORM_PLAIN, "7/1,6/1"))
+    assert [sum(p["sub_log"]) for p in s["passes"]] == [7, 6] and s["passes"][0]["sub_log"] == [1] * 7
+    assert "8/1,8/1" in M.fft_tune_candidates(1 << 16, M.FFT_C64)
 

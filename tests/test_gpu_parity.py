@@ -122,7 +122,8 @@ def test_adjoint(dt, direction, t):
 
 @pytest.mark.parametrize("dt", [M.FFT_C128, M.FFT_C64])
 @pytest.mark.parametrize("schedule", ["4,4,4", "6,6", "2,3,3,4", "1,11", "12@2", "4@16,4@2,4@4",
-                                      "3,3,3,3;chunk=2", "11,1", "5,7;chunk=3"])
+                                      "3,3,3,3;chunk=2", "11,1", "5,7;chunk=3",
+                                      "6/1,6/1", "6/2,6/3", "7/3,5/2", "12/2"])
 def test_forced_schedules(dt, schedule):
     n = 1 << 12
     x = W.uniform_complex(n, 7, seed=3)
