@@ -161,9 +161,12 @@ def recorded_traffic(kernel: str, workload_key: str):
     return e.get("bytes_per_launch")
 
 
-def cpu_baseline(n: int, batch: int, target_s: float = 12.0):
+def cpu_baseline(n: int, batch: int, target_s: float = 12.0, rows=None):
     """Time the FP64 oracle (as it stands) on the host cores on a bounded
-    sample of the workload: forward + inverse of S transforms."""
+    sample of the workload: forward + inverse of S transforms.  With rows (a
+    function s -> (input rows, the GPU's forward spectrum of those rows)),
+    the sample is the bench's own first S transforms and the oracle's
+    spectrum is also the parity check of the timed GPU output."""
     import numpy as np
     import oracle as O
     import workloads as W
@@ -175,15 +178,23 @@ def cpu_baseline(n: int, batch: int, target_s: float = 12.0):
     s = int(min(batch, max(cores, math.ceil(target_s / (2 * t1)))))
     s = max(1, min(batch, (s // cores) * cores if s >= cores else s))
     threads = min(cores, s)
-    x = W.uniform_complex(n, s, seed=0)
+    if rows is not None:
+        x, Xg = rows(s)
+    else:
+        x, Xg = W.uniform_complex(n, s, seed=0), None
     t0 = time.perf_counter()
     X = O.fft(x, "forward", c=1024, threads=threads)
     O.fft(X, "inverse", c=1024, threads=threads)
     dt = time.perf_counter() - t0
     gflops = 2 * 5.0 * n * math.log2(n) * s / dt / 1e9
-    return {"value": round(gflops, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{s} of the {batch} transforms of n=2^{int(math.log2(n))}, forward+inverse, "
-                      f"{threads} threads, {dt:.2f} s wall"}
+    out = {"value": round(gflops, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{s} of the {batch} transforms of n=2^{int(math.log2(n))}, forward+inverse, "
+                     f"{threads} threads, {dt:.2f} s wall"}
+    if Xg is not None:
+        err = np.linalg.norm(Xg - X, axis=-1) / np.linalg.norm(X, axis=-1)
+        out["gpu_vs_oracle_rel_err"] = {"transforms": int(s), "max": float(err.max()),
+                                        "median": float(np.median(err)), "tolerance": 1e-12}
+    return out
 
 
 # --------------------------------------------------------------- reference
@@ -338,7 +349,10 @@ def run_moafft(args):
                 "roundtrip_rel_err": rt, "clocks": clocks, "roofline": roofline, "e2e": e2e,
                 "forms": forms}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(n, batch)
+            fwd.exec(x, X, stream)  # the timed forward spectrum (deterministic)
+            torch.cuda.synchronize()
+            line["cpu_baseline"] = cpu_baseline(
+                n, batch, rows=lambda s: (x[:s].cpu().numpy(), X[:s].cpu().numpy()))
         print(json.dumps(line), flush=True)
 
     for t in [int(v) for v in args.sweep.split(",") if v.strip()]:
@@ -406,7 +420,8 @@ def measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, wor
 
 def sweep_line(M, torch, dev, stream, log2n, args):
     n, batch = workload(log2n)
-    x = torch.rand(batch, n, dtype=torch.complex128, device=dev) * 2 - (1 + 1j)
+    gen = torch.Generator(device=dev).manual_seed(log2n)
+    x = torch.rand(batch, n, dtype=torch.complex128, device=dev, generator=gen) * 2 - (1 + 1j)
     X = torch.empty_like(x)
     y = torch.empty_like(x)
     fwd = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD)
@@ -425,8 +440,10 @@ def sweep_line(M, torch, dev, stream, log2n, args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / k
+    rt = (torch.linalg.vector_norm((y - x).flatten()) / torch.linalg.vector_norm(x.flatten())).item()
     print(json.dumps({"sweep": True, "n": n, "batch": batch, "ms_per_step": round(ms, 4),
-                      "gflops": round(flops_per_step(n, batch) / (ms * 1e-3) / 1e9, 2)}),
+                      "gflops": round(flops_per_step(n, batch) / (ms * 1e-3) / 1e9, 2),
+                      "roundtrip_rel_err": rt}),
           file=sys.stderr, flush=True)
     fwd.close()
     inv.close()
