@@ -467,6 +467,10 @@ struct fft_plan_s {
     int n_ctr = 0;
     DevBuf d_segs, d_queue, d_ctr;
     cudaStream_t s_capture = nullptr;
+    // a second captured branch: the single-pass classes (which need no
+    // workspace) run beside the multi-pass ones, which share the workspace
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void *g_in = nullptr;
     void *g_out = nullptr;
@@ -640,6 +644,9 @@ static void destroy_plan(fft_plan_s *p)
     if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->s_capture) cudaStreamDestroy(p->s_capture);
+    if (p->s_aux) cudaStreamDestroy(p->s_aux);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (auto &r : p->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1115,6 +1122,9 @@ static int exec_graph(fft_plan_t p, const void *in, void *out, int sign, cudaStr
         }
         cudaError_t e = cudaSuccess;
         if (!p->s_capture) e = cudaStreamCreateWithFlags(&p->s_capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !p->s_aux) e = cudaStreamCreateWithFlags(&p->s_aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail_cuda(e, "capture stream");
         std::vector<PersistSeg> segs;
         long long total = 0;
@@ -1143,7 +1153,19 @@ static int exec_graph(fft_plan_t p, const void *in, void *out, int sign, cudaStr
             }
             if (e2 != cudaSuccess) st = fail_cuda(e2, "persistent launch");
         } else {
-            st = exec_all(p, in, out, sign, p->s_capture);
+            // fork: single-pass classes on the second branch, the others
+            // (sharing the workspace) in order on the first; join at the end
+            cudaError_t e2 = cudaEventRecord(p->ev_fork, p->s_capture);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(p->s_aux, p->ev_fork, 0);
+            if (e2 != cudaSuccess) st = fail_cuda(e2, "graph fork");
+            for (const auto &c : p->classes) {
+                if (st != FFT_OK) break;
+                const bool single = !c.sched.unblocked && c.sched.npass == 1;
+                st = exec_class(p, c, in, out, 0, c.count, sign, single ? p->s_aux : p->s_capture);
+            }
+            e2 = cudaEventRecord(p->ev_join, p->s_aux);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(p->s_capture, p->ev_join, 0);
+            if (e2 != cudaSuccess && st == FFT_OK) st = fail_cuda(e2, "graph join");
         }
         p->profile = prof;
         cudaGraph_t g = nullptr;
