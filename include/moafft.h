@@ -91,10 +91,18 @@ int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir di
  * autotuner choice); "auto" runs the autotuner now (times candidate
  * schedules on the plan's own buffers, then caches the winner).  Otherwise
  * the string lists the log2 radix of each HBM pass, comma separated, each
- * optionally followed by "@W" (columns per thread block), e.g. "10,10" or
- * "8@8,8@8,8@8".  The radices must sum to log2 n.  The paper lets the user
- * choose the block size c at run time (Ch.2 "specify the blocking size at
- * run time"); a pass of log2 radix r is a group of r radix-2 stages. */
+ * optionally followed by "@W" (columns per thread block) and "/k" (register
+ * digits of at most 2^k points, k = 1..4, default 4: the general radix of
+ * Fig. radnbutterfly), e.g. "10,10", "8@8,8@8,8@8" or "8/2,8/2".  The
+ * radices must sum to log2 n.  Options after ';': "chunk=K" (transforms per
+ * workspace round of a multi-pass plan).  Special schedules: "stages" (the
+ * unblocked routine: a bit reversal, then one HBM pass per radix-2 stage,
+ * Fig. fftpsirad2) and "cluster" (complex64, n = 2^16, plain form only: one
+ * HBM round trip, the reshape-transpose carried by the distributed shared
+ * memory of a thread-block cluster; FFT_ERR_UNSUPPORTED elsewhere).  The
+ * paper lets the user choose the block size c at run time (Ch.2 "specify
+ * the blocking size at run time"); a pass of log2 radix r is a group of r
+ * radix-2 stages. */
 int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,
                 fft_form form, const char *schedule);
 
