@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64"],
+    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64", "dm"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -686,6 +686,16 @@ def run_case(args):
     """A small case for ncu captures of the complex64 kernels."""
     import torch
     import paper_0803_2386_gb300 as M
+    if args.case == "dm":  # density-matrix gate: 13 qubits, complex64 (512 MiB), qubit 0
+        import numpy as np
+        gen = torch.Generator(device="cuda").manual_seed(13)
+        rho = torch.randn(1 << 13, 1 << 13, dtype=torch.complex64, device="cuda", generator=gen)
+        u = np.linalg.qr(np.random.default_rng(0).standard_normal((2, 2)))[0].astype(np.complex128)
+        for _ in range(3):
+            M.dm_gate(rho, [0], u)
+        torch.cuda.synchronize()
+        print("ok")
+        return 0
     form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
             "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN,
             "c64_rows": M.FFT_FORM_PLAIN, "c1": M.FFT_FORM_PLAIN}[args.case]
