@@ -2,7 +2,7 @@
 //
 // A codelet of size E = 2^k performs k radix-2 stages on E values held in
 // registers: the innermost level of the memory hierarchy, where the paper's
-// "block of length c" (Ch.3) is the register file of one thread.  Each
+// block of c points (Ch.3) is the register file of one thread.  Each
 // codelet splits its input index top digit first, n = (E/4)*n0 + n1, does
 // the small DFTs over n0, multiplies by w_E^(n1*k0) and finishes with DFTs
 // over n1 (the same recursion the passes use at the HBM and shared-memory

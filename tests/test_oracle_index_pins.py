@@ -184,9 +184,9 @@ def test_final_transpose_undoes_all_reshape_transposes(t):
 
 def test_schedule_examples():
     # n = 32, c = 4: two reshape-transposes, one final stage (Sec.
-    # butter-order: "only cycles of length 2" after the last transpose)
+    # butter-order: after the last transpose only 2-cycles remain)
     assert O.schedule(32, 4) == (2, 2, 1)
-    # c >= n: the unblocked routine ("same code with c >= n")
+    # c >= n: the unblocked routine (the blocked code with c >= n)
     assert O.schedule(32, 64) == (6, 0, 5)
     assert O.schedule(32, 32) == (5, 0, 5)
     # n = 2^pmax * c^lmax with 1 <= pmax <= log2 c
