@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.  Tolerances (relative L2 per transform): FP64 path
 1e-12; FP32 path 1e-6 * log2 n."""
+import json
+
 import numpy as np
 import pytest
 
@@ -242,3 +244,21 @@ def test_unblocked_stages(dt, t):
     assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, True)).max() <= tol(dt, n)
     y = run_plan(x, dt, M.FFT_FORWARD, schedule="stages", inplace=True)
     assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, False)).max() <= tol(dt, n)
+
+
+def test_latency_schedule_for_tiny_batches():
+    """A few small transforms take two passes one column / row wide (many
+    thread blocks instead of one tile with idle rows); larger batches keep the
+    tile passes."""
+    p = M.fft_plan(1 << 10, 1, M.FFT_C128, M.FFT_FORWARD)
+    try:
+        s = json.loads(M.fft_plan_describe(p))["schedule"]
+    finally:
+        M.fft_destroy(p)
+    assert [q["log_r"] for q in s["passes"]] == [5, 5] and [q["width"] for q in s["passes"]] == [1, 1]
+    p = M.fft_plan(1 << 10, 64, M.FFT_C128, M.FFT_FORWARD)
+    try:
+        s = json.loads(M.fft_plan_describe(p))["schedule"]
+    finally:
+        M.fft_destroy(p)
+    assert [q["log_r"] for q in s["passes"]] == [10]
