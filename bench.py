@@ -521,9 +521,31 @@ def extra_configs(M, torch, dev, stream):
         _emit({"config": f"c64 {name} n=2^16 batch 4096 forward", "ms": round(ms, 3),
                "gflops": round(fl / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
                "hbm_frac_of_measured": round(gbs / hbm, 4) if hbm else None,
-               "rel_err_vs_fp64": rel(out, ref), "speedup_vs_fp64": round(ms64 / ms, 2)})
+               "rel_err_vs_fp64": rel(out, ref), "speedup_vs_fp64": round(ms64 / ms, 2),
+               "tolerance": 1e-6 * 16 if form == M.FFT_FORM_PLAIN else 1e-5 * 16})
         pf.close()
     del ref, out, xc
+    # the same forms on the dynamic-range input (amplitudes 10^U(-4, 4), seed 0)
+    nb = 256
+    xd = torch.from_numpy(W.dynamic_range_complex(n, nb, seed=0)).to(dev)
+    refd = torch.empty_like(xd)
+    p64 = M.Plan(n, nb, M.FFT_C128, M.FFT_FORWARD)
+    p64.exec(xd.to(torch.complex64).to(torch.complex128), refd, stream)
+    p64.close()
+    xd64 = xd.to(torch.complex64)
+    outd = torch.empty_like(xd64)
+    row = {"config": f"c64 precision forms, dynamic range 1e-4..1e4, n=2^16 batch {nb} forward (error vs FP64 path)"}
+    for form, name in ((M.FFT_FORM_PLAIN, "fp32"), (M.FFT_FORM_TC_FP16, "tc_fp16"), (M.FFT_FORM_TC_BF16, "tc_bf16")):
+        pf = M.Plan(n, nb, M.FFT_C64, M.FFT_FORWARD, form)
+        pf.exec(xd64, outd, stream)
+        torch.cuda.synchronize()
+        M.fft_plan_check(pf.handle)
+        row[f"{name}_rel_err"] = rel(outd, refd)
+        pf.close()
+    row["tolerance_fp32"] = 1e-6 * 16
+    row["tolerance_tc"] = 1e-5 * 16
+    _emit(row)
+    del xd, refd, xd64, outd
 
     # uneven batch: 20,000 complex64 transforms, n in 2^6..2^16 (seed 1)
     sizes, data = W.uneven_batch()
