@@ -269,11 +269,12 @@ static int build_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
         s.cluster = true;
         return st;
     }
-    if (body == "stages") {
+    if (body == "stages" || body == "stages_stride") {
         s = Schedule();
         s.n = n;
         s.t = exact_log2(n);
         s.unblocked = true;
+        s.stride_order = body == "stages_stride";
         s.npass = 0;
         return FFT_OK;
     }
@@ -283,7 +284,8 @@ static int build_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text
 static std::string schedule_json(const Schedule &s)
 {
     if (s.unblocked)
-        return "{\"n\": " + std::to_string(s.n) + ", \"unblocked\": true, \"stages\": " + std::to_string(s.t) +
+        return "{\"n\": " + std::to_string(s.n) + ", \"unblocked\": true, \"order\": \"" +
+               (s.stride_order ? "stride" : "onf") + "\", \"stages\": " + std::to_string(s.t) +
                ", \"passes\": []}";
     std::string j = "{\"n\": " + std::to_string(s.n) + (s.cluster ? ", \"cluster\": true" : "") + ", \"passes\": [";
     for (int i = 0; i < s.npass; i++) {
@@ -1026,7 +1028,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
         if (ragged) return fail(FFT_ERR_UNSUPPORTED, "the per-stage schedule takes dense batches");
         const char *src = (const char *)in + (size_t)t0 * C.n * eb;
         char *dst = (char *)out + (size_t)t0 * C.n * eb;
-        cudaError_t e = launch_stages(p->dt == FFT_C128, src, dst, p->ws.ptr, C.n, cnt,
+        cudaError_t e = launch_stages(p->dt == FFT_C128, S.stride_order, src, dst, p->ws.ptr, C.n, cnt,
                                       (const char *)p->tw.ptr + S.pass[0].tw_pass_off * eb, sign, scale, s);
         if (e != cudaSuccess) return fail_cuda(e, "per-stage launch");
         return FFT_OK;

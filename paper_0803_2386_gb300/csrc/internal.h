@@ -45,6 +45,7 @@ struct Schedule {
     // stage after a bit-reversal pass (stages.cu); pass[0].tw_pass_off then
     // locates the table w_n^e, e < n/2
     bool unblocked = false;
+    bool stride_order = false;  // "stages_stride": the same pairs in power-of-two stepping order
     // schedule "cluster" (complex64, n = 2^16): one launch whose 8-CTA
     // clusters keep a whole transform in distributed shared memory
     // (cluster_kernel.cu); pass[0].tw_pass_off then locates the direct table
@@ -117,8 +118,8 @@ cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total
 
 // unblocked per-stage transform (stages.cu); tmp (n * count elements) is
 // used when in == out
-cudaError_t launch_stages(bool f64, const void *in, void *out, void *tmp, int64_t n, int64_t count, const void *tw,
-                          int dir, double scale, cudaStream_t s);
+cudaError_t launch_stages(bool f64, bool stride, const void *in, void *out, void *tmp, int64_t n, int64_t count,
+                          const void *tw, int dir, double scale, cudaStream_t s);
 
 // one-round-trip complex64 transforms of n = 2^cluster_log2n() through
 // thread-block clusters (cluster_kernel.cu); cudaErrorNotSupported when the

@@ -9,6 +9,13 @@
 //     a = Z[m*g + nn],  d = Z[m*g + f + nn],  0 <= nn < f,
 // and updates them to (a + w*d, a - w*d) with w = w_g^nn (the weight the
 // ONF assumes applied beforehand).
+//
+// Two orders of the same pairs (Ch.5 compares its loop orders and
+// conjectures that the unit-stride one wins): ONF (consecutive threads take
+// consecutive nn: unit-stride accesses, one weight per thread) and STRIDE
+// (consecutive threads take consecutive m with nn fixed: accesses g points
+// apart, the weight shared -- the power-of-two stepping order of the
+// classic loop nest).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,7 +37,7 @@ __global__ void bitrev_kernel(const typename cvec<T>::type *in, typename cvec<T>
     }
 }
 
-template <typename T, int DIR>
+template <typename T, int DIR, bool STRIDE>
 __global__ void stage_kernel(const typename cvec<T>::type *src, typename cvec<T>::type *dst, int64_t n, int t,
                              int j, int64_t pairs, const typename cvec<T>::type *tw, T scale)
 {
@@ -41,7 +48,9 @@ __global__ void stage_kernel(const typename cvec<T>::type *src, typename cvec<T>
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t tr = p >> half_log;
         const int64_t q = p & (((int64_t)1 << half_log) - 1);
-        const int64_t m = q >> j, nn = q & (f - 1);
+        // q enumerates the n/2 pairs (m, nn), m < n/g, nn < f
+        const int64_t m = STRIDE ? (q & ((((int64_t)1) << (half_log - j)) - 1)) : (q >> j);
+        const int64_t nn = STRIDE ? (q >> (half_log - j)) : (q & (f - 1));
         const int64_t i0 = tr * n + (m << (j + 1)) + nn, i1 = i0 + f;
         const V a = src[i0];
         V d = src[i1];
@@ -65,7 +74,7 @@ static int grid_of(int64_t work)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T>
+template <typename T, bool STRIDE>
 static cudaError_t run_stages(const void *in, void *out, void *tmp, int64_t n, int64_t count, const void *tw,
                               int dir, double scale, cudaStream_t s)
 {
@@ -87,20 +96,23 @@ static cudaError_t run_stages(const void *in, void *out, void *tmp, int64_t n, i
         V *dst = last ? (V *)out : first;
         const T sc = last ? (T)scale : (T)1;
         if (dir < 0)
-            stage_kernel<T, -1><<<grid_of(pairs), 256, 0, s>>>(first, dst, n, t, j, pairs, (const V *)tw, sc);
+            stage_kernel<T, -1, STRIDE><<<grid_of(pairs), 256, 0, s>>>(first, dst, n, t, j, pairs, (const V *)tw, sc);
         else
-            stage_kernel<T, 1><<<grid_of(pairs), 256, 0, s>>>(first, dst, n, t, j, pairs, (const V *)tw, sc);
+            stage_kernel<T, 1, STRIDE><<<grid_of(pairs), 256, 0, s>>>(first, dst, n, t, j, pairs, (const V *)tw, sc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_stages(bool f64, const void *in, void *out, void *tmp, int64_t n, int64_t count, const void *tw,
-                          int dir, double scale, cudaStream_t s)
+cudaError_t launch_stages(bool f64, bool stride, const void *in, void *out, void *tmp, int64_t n, int64_t count,
+                          const void *tw, int dir, double scale, cudaStream_t s)
 {
-    return f64 ? run_stages<double>(in, out, tmp, n, count, tw, dir, scale, s)
-               : run_stages<float>(in, out, tmp, n, count, tw, dir, scale, s);
+    if (stride)
+        return f64 ? run_stages<double, true>(in, out, tmp, n, count, tw, dir, scale, s)
+                   : run_stages<float, true>(in, out, tmp, n, count, tw, dir, scale, s);
+    return f64 ? run_stages<double, false>(in, out, tmp, n, count, tw, dir, scale, s)
+               : run_stages<float, false>(in, out, tmp, n, count, tw, dir, scale, s);
 }
 
 }  // namespace moafft

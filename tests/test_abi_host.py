@@ -134,7 +134,9 @@ def test_tune_candidates_are_valid_schedules(t, dt):
 
 def test_unblocked_schedule_describes_stages():
     s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "stages"))
-    assert s["unblocked"] and s["stages"] == 12 and s["passes"] == []
+    assert s["unblocked"] and s["stages"] == 12 and s["passes"] == [] and s["order"] == "onf"
+    s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "stages_stride"))
+    assert s["unblocked"] and s["order"] == "stride"
 
 
 def test_cluster_schedule_describes_two_groups():

@@ -229,20 +229,22 @@ def test_full_size_c64_sampled():
 
 # ------------------------------------- unblocked routine (one pass per stage)
 
+@pytest.mark.parametrize("order", ["stages", "stages_stride"])
 @pytest.mark.parametrize("dt", [M.FFT_C128, M.FFT_C64])
 @pytest.mark.parametrize("t", [0, 1, 2, 5, 10, 13])
-def test_unblocked_stages(dt, t):
-    """Schedule "stages": bit reversal, then one HBM pass per radix-2 stage
-    with the hyper-cube ONF pairs (the paper's fftpsirad2 on the GPU)."""
+def test_unblocked_stages(dt, t, order):
+    """Schedules "stages" / "stages_stride": bit reversal, then one HBM pass
+    per radix-2 stage with the hyper-cube ONF pairs, taken in unit-stride or
+    in power-of-two stepping order (the paper's fftpsirad2 on the GPU)."""
     n = 1 << t
     x = W.uniform_complex(n, 3, seed=200 + t)
     xr = rounded(x, dt)
     for direction in (M.FFT_FORWARD, M.FFT_INVERSE):
-        y = run_plan(x, dt, direction, schedule="stages")
+        y = run_plan(x, dt, direction, schedule=order)
         assert rel_rows(y, oracle_op(xr, direction, False)).max() <= tol(dt, n)
-    y = run_plan(x, dt, M.FFT_FORWARD, adjoint=True, schedule="stages")
+    y = run_plan(x, dt, M.FFT_FORWARD, adjoint=True, schedule=order)
     assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, True)).max() <= tol(dt, n)
-    y = run_plan(x, dt, M.FFT_FORWARD, schedule="stages", inplace=True)
+    y = run_plan(x, dt, M.FFT_FORWARD, schedule=order, inplace=True)
     assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, False)).max() <= tol(dt, n)
 
 
