@@ -138,9 +138,11 @@ int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream)
  * staged by the driver).  The batch is streamed through device staging
  * buffers the plan allocates on first use (two slots of up to 64 MiB each):
  * host-to-device copy, transform and device-to-host copy of consecutive
- * slices overlap on the plan's own copy streams.  The call returns after
- * enqueueing; `cuda_stream` waits for the last copy, so synchronising it
- * makes `out` valid.  in == out is allowed.  The paper times whole
+ * slices overlap on the plan's own copy streams.  Stream-ordered: the
+ * copies start after the work already queued on `cuda_stream` (so a call may
+ * read the output of the previous host call on that stream), and
+ * `cuda_stream` waits for the last copy, so synchronising it makes `out`
+ * valid.  The call returns after enqueueing.  in == out is allowed.  The paper times whole
  * executables including data movement (Ch.1 "Experiments"); this is that
  * end-to-end path. */
 int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream);

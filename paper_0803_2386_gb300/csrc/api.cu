@@ -460,6 +460,7 @@ struct fft_plan_s {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
                 ev_d2h[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr;  // the caller's stream at the start of a host call
     // uneven plans replay one captured graph per (in, out, adjoint)
     bool use_graph = false;
     // ... whose body is one persistent kernel when every class fits it
@@ -641,6 +642,7 @@ static void destroy_plan(fft_plan_s *p)
         if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
         if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
     }
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
     if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
@@ -1267,6 +1269,7 @@ static int setup_staging(fft_plan_t p)
     }
     cudaError_t e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; k++) {
         e = cudaEventCreateWithFlags(&p->ev_h2d[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming);
@@ -1293,6 +1296,14 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
     cudaStream_t cs = (cudaStream_t)stream;
     bool used[2] = {false, false};
     const SizeClass &C = p->classes[0];
+    // stream order: the copies start after the work already queued on the
+    // caller's stream (for instance a previous host call whose output this
+    // call reads)
+    {
+        cudaError_t e = cudaEventRecord(p->ev_start, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_h2d, p->ev_start, 0);
+        if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (stream order)");
+    }
     for (int64_t b0 = 0, i = 0; b0 < p->batch; b0 += p->stage_tr, i++) {
         int k = (int)(i & 1);
         int64_t cnt = std::min(p->stage_tr, p->batch - b0);

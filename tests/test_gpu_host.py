@@ -90,3 +90,26 @@ def test_rejects_uneven_plans_and_device_pointers():
         assert e.value.status == M.FFT_ERR_ARG
     finally:
         M.fft_destroy(p)
+
+
+def test_chained_calls_are_stream_ordered():
+    """Forward then inverse through host buffers on one stream, the second
+    call reading the first call's output, with no synchronisation between
+    them: the second call's copies start after the first call's work."""
+    n, batch = 1 << 16, 512
+    x = W.uniform_complex(n, batch, seed=73).astype(np.complex64)
+    xin = torch.from_numpy(x).pin_memory()
+    mid = torch.empty_like(xin).pin_memory()
+    back = torch.empty_like(xin).pin_memory()
+    pf = M.fft_plan(n, batch, M.FFT_C64, M.FFT_FORWARD)
+    pi = M.fft_plan(n, batch, M.FFT_C64, M.FFT_INVERSE)
+    try:
+        s = torch.cuda.Stream()
+        M.fft_exec_host(pf, xin, mid, s)
+        M.fft_exec_host(pi, mid, back, s)
+        s.synchronize()
+    finally:
+        M.fft_destroy(pf)
+        M.fft_destroy(pi)
+    err = rel_rows(back.numpy().astype(np.complex128), x.astype(np.complex128))
+    assert err.max() <= 1e-6 * 16
