@@ -264,3 +264,16 @@ def test_latency_schedule_for_tiny_batches():
     finally:
         M.fft_destroy(p)
     assert [q["log_r"] for q in s["passes"]] == [10]
+
+
+@pytest.mark.parametrize("t", [22, 24])
+def test_large_complex64_three_passes(t):
+    """Large complex64 transforms (2^22: two passes of 2^11, 2^24: three of
+    2^8; pass weights split by the digits of k), every transform against the
+    oracle."""
+    n = 1 << t
+    batch = 2
+    x = W.uniform_complex(n, batch, seed=60 + t)
+    y = run_plan(x, M.FFT_C64)
+    ref = O.fft(rounded(x, M.FFT_C64), "forward", c=4096, threads=2)
+    assert rel_rows(y, ref).max() <= 1e-6 * t
