@@ -430,6 +430,7 @@ struct SizeClass {
     int64_t chunk = 1;           // transforms per workspace round
     std::vector<int64_t> offs;   // element offsets (uneven plans)
     bool off_even = true;        // every offset a multiple of 2 points
+    int64_t off_align = 1024;    // largest power of two (<= 1024) dividing every offset
     DevBuf d_off;                // the same on the device
 };
 
@@ -690,7 +691,11 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
         }
         if (!c.offs.empty()) {
             c.off_even = true;
-            for (int64_t o : c.offs) c.off_even = c.off_even && (o % 2 == 0);
+            c.off_align = 1024;
+            for (int64_t o : c.offs) {
+                c.off_even = c.off_even && (o % 2 == 0);
+                while (c.off_align > 1 && o % c.off_align) c.off_align >>= 1;
+            }
             int st = dev_alloc(c.d_off, c.offs.size() * sizeof(int64_t), "offset table");
             if (st != FFT_OK) return st;
             e = cudaMemcpy(c.d_off.ptr, c.offs.data(), c.offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -1076,6 +1081,8 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.in_off = (i == 0) ? off : nullptr;
             a.out_off = (i == S.npass - 1) ? off : nullptr;
             a.off_even = C.off_even ? 1 : 0;
+            a.off_align = C.off_align;
+            a.total_elems = ragged ? p->total : 0;
             a.count = c;
             a.log_r = d.log_r;
             a.width = d.width;

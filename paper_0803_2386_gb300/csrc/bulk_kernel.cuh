@@ -90,13 +90,21 @@ __device__ __forceinline__ void bulk_issue(const PassArgs &p, const CUtensorMap 
         const int64_t rem = cta - tr * tiles_per_tr;
         const int64_t a = rem / colgroups;
         const int64_t b0 = (rem - a * colgroups) * W;
-        // rows of the 2-D view: (tr * A + a) * R + m, columns b
+        // rows of the 2-D view of B points: dense batches (tr * A + a) * R + m;
+        // ragged ones start at in_off[tr] (a multiple of W, so the W columns
+        // of a box never straddle a row of the view)
         constexpr int BR = R < 256 ? R : 256;
         if (lane == 0) {
             tc::mbar_arrive_expect_tx(mbar, (uint32_t)(R * W * sizeof(float2)));
-            const int y0 = (int)((tr * p.A + a) * R);
+            int x0 = (int)b0;
+            int64_t y0 = (tr * p.A + a) * R;
+            if (p.in_off) {
+                const int64_t e0 = p.in_off[tr] + a * (int64_t)R * p.B + b0;
+                x0 = (int)(e0 % p.B);
+                y0 = e0 / p.B;
+            }
             for (int k = 0; k < R / BR; k++)
-                tc::tensor_g2s_2d(stage + (size_t)k * BR * W, tmap, (int)b0, y0 + k * BR, mbar);
+                tc::tensor_g2s_2d(stage + (size_t)k * BR * W, tmap, x0, (int)(y0 + k * BR), mbar);
         }
         (void)in;
     } else {

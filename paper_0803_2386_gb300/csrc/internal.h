@@ -88,6 +88,8 @@ struct PassArgs {
     const int64_t *in_off;
     const int64_t *out_off;
     int off_even;  // every offset is a multiple of 2 points (16-byte rows)
+    int64_t off_align;    // largest power of two (<= 1024) dividing every offset
+    int64_t total_elems;  // ragged batches: points in the packed buffer
     // device word set to 1 when a bounded wait inside a kernel gave up
     int *err;
     // tensor-core form: the split 32x32 DFT matrix of this direction, hi

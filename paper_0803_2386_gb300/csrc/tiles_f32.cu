@@ -67,7 +67,10 @@ static bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map)
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const int R = 1 << a.log_r;
-    cuuint64_t dims[2] = {(cuuint64_t)a.B, (cuuint64_t)(a.count * a.A * R)};
+    // ragged batches: the whole packed buffer as rows of B points (the last
+    // row may be partial; boxes only touch columns of their own transform)
+    const int64_t rows = a.in_off ? (a.total_elems + a.B - 1) / a.B : a.count * a.A * R;
+    cuuint64_t dims[2] = {(cuuint64_t)a.B, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)a.B * 8};
     cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)(R < 256 ? R : 256)};
     cuuint32_t estr[2] = {1, 1};
@@ -152,8 +155,10 @@ cudaError_t launch_tile_f32(const PassArgs &a, int dir, cudaStream_t s)
     // column tiles by 2-D tensor-map boxes; dense, 16-byte aligned input
     static const bool bulk = getenv("MOAFFT_NO_BULK") == nullptr;
     static const bool cols = getenv("MOAFFT_NO_TMA_COLUMNS") == nullptr;
-    // ragged (uneven) inputs: single-pass rows whose offsets keep 16-byte rows
-    const bool dense_in = a.in_off == nullptr || (a.is_last && a.A == 1 && a.off_even);
+    // ragged (uneven) inputs: single-pass rows whose offsets keep 16-byte
+    // rows, and column tiles whose offsets are multiples of the tile width
+    const bool dense_in = a.in_off == nullptr || (a.is_last ? (a.A == 1 && a.off_even)
+                                                            : (a.total_elems > 0 && a.off_align % a.width == 0));
     if (bulk && (a.is_last || cols) && bulk_ok(a.log_r, a.is_last) && dense_in && ((uintptr_t)a.in % 16) == 0) {
         cudaError_t e;
         if (dir < 0) e = a.is_last ? launch_bulk_dir<-1, true>(a, s) : launch_bulk_dir<-1, false>(a, s);
