@@ -122,7 +122,6 @@ static int exact_log2(int64_t n)
 
 // elements a tile may hold (shared memory budget of 64 KiB per CTA)
 static int tile_budget(fft_dtype dt) { return dt == FFT_C128 ? 4096 : 8192; }
-static int max_tile_log(fft_dtype dt) { return dt == FFT_C128 ? 11 : 11; }
 static size_t elem_bytes(fft_dtype dt) { return dt == FFT_C128 ? 16 : 8; }
 
 // register digits of at most max_digit bits, the remainder first (the
@@ -194,8 +193,34 @@ static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
     s = Schedule();
     s.n = n;
     s.t = exact_log2(n);
-    int mt = max_tile_log(dt);
-    int g = s.t == 0 ? 1 : (s.t + mt - 1) / mt;
+    // up to 2^12 points: one pass (the whole transform is one tile)
+    if (s.t <= 12) {
+        s.npass = 1;
+        s.pass[0].log_r = s.t;
+        return finish_schedule(s, dt, nullptr);
+    }
+    // complex64 passes are HBM-bound, and the narrow column tiles of radices
+    // above 2^10 (width 2 or 1) waste DRAM sectors: a third pass of <= 2^10
+    // points costs less than one such pass.  The splits are the fastest of
+    // an exhaustive sweep of two- and three-pass schedules on GB300 (1 GiB
+    // batches), the smaller radix first where the order mattered.
+    static const char *const c64_split[] = {
+        "7,6",   "7,7",    "7,8",    "8,8",   "8,9",   "8,10",  // 2^13 .. 2^18
+        "9,10",  "10,10",  "7,7,7",  "7,7,8", "7,8,8", "8,8,8"  // 2^19 .. 2^24
+    };
+    if (dt == FFT_C64 && s.t >= 13 && s.t <= 24) {
+        const char *sp = c64_split[s.t - 13];
+        s.npass = 0;
+        for (const char *c = sp; *c;) {
+            s.pass[s.npass++].log_r = (int)strtol(c, const_cast<char **>(&c), 10);
+            if (*c == ',') c++;
+        }
+        return finish_schedule(s, dt, nullptr);
+    }
+    // otherwise balanced passes of at most 2^11 (complex128: FP64-bound, the
+    // split matters little) / 2^10 (complex64) points
+    const int mt = dt == FFT_C128 ? 11 : 10;
+    const int g = (s.t + mt - 1) / mt;
     s.npass = g;
     for (int i = 0; i < g; i++) s.pass[i].log_r = s.t / g + (i < s.t % g ? 1 : 0);
     return finish_schedule(s, dt, nullptr);
@@ -549,6 +574,8 @@ static int make_tables(fft_plan_s *p)
             PassDesc &d = c.sched.pass[i];
             d.tw_tile_off = off;
             off += (size_t)1 << d.log_r;
+            d.tw_digit_off = off;
+            off += (size_t)digit_table_entries(d.log_r);
             if (i < c.sched.npass - 1) {
                 d.tw_pass_off = off;
                 if (d.tw_mode == 3) {
@@ -594,6 +621,7 @@ static int make_tables(fft_plan_s *p)
             const size_t wb = p->form == FFT_FORM_DF64 ? 16 : eb;
             char *arena = (char *)p->tw.ptr;
             cudaError_t e = gen(d.tw_tile_off, R, R, 1);
+            if (e == cudaSuccess) e = launch_digit_tables(arena + d.tw_digit_off * wb, kind, d.log_r, 0);
             if (e == cudaSuccess && i < c.sched.npass - 1) {
                 if (d.tw_mode == 2) {
                     e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, R, d.B, d.tw_m, 1, 0);
@@ -863,6 +891,7 @@ static void fill_args(const fft_plan_s *p, const SizeClass &C, int i, PassArgs &
     a.B = d.B;
     a.is_last = (i == C.sched.npass - 1);
     a.tw_tile = (const char *)p->tw.ptr + d.tw_tile_off * eb;
+    a.tw_digit = (const char *)p->tw.ptr + d.tw_digit_off * eb;
     a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
     a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
     a.tw_lo_bits = d.tw_lo_bits;
@@ -1092,6 +1121,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.B = d.B;
             a.is_last = (i == S.npass - 1);
             a.tw_tile = (const char *)p->tw.ptr + d.tw_tile_off * eb;
+            a.tw_digit = (const char *)p->tw.ptr + d.tw_digit_off * eb;
             a.tw_pass = (const char *)p->tw.ptr + d.tw_pass_off * eb;
             a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
             a.tw_lo_bits = d.tw_lo_bits;

@@ -34,6 +34,7 @@ struct PassDesc {
     size_t tw_tile_off = 0;      // element offsets into the plan's twiddle arena
     size_t tw_pass_off = 0;
     size_t tw_hi_off = 0;
+    size_t tw_digit_off = 0;
 };
 
 struct Schedule {
@@ -70,6 +71,9 @@ struct PassArgs {
     int npass;                  // passes of the whole schedule
     int pass_log[kMaxPasses];   // their log2 radices (for the final transpose)
     const void *tw_tile;        // w_R^e, e < R
+    // the tile kernels' weights between register digits, one table per
+    // digit level with rows by the codelet output k (digit_table_entries)
+    const void *tw_digit;
     // Pass weights w_M^(b k), M = R B, b < B the column, k < R the tile
     // index, in one of these layouts (tw_mode):
     //   0: indexed by e = b k: tw_pass = w_M^e (tw_lo_bits = 0) or the
@@ -159,6 +163,27 @@ cudaError_t launch_twiddle_df64(float *dst, int64_t count, int64_t m, int64_t st
 // c < cols; kind 0 complex128, 1 complex64, 2 double-float pairs
 cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, int64_t m, int64_t rstep,
                               cudaStream_t s);
+// Weights between the register digits of a tile of R = 2^log_r points
+// (4 <= log_r <= 12; the split of tile_kernel.cuh: a first digit of E0
+// points over Q0 = R / E0, then radix-16 digits), stored level by level with
+// rows by the codelet output k, so that a warp's consecutive codelets read
+// consecutive entries:
+//   level 0:  T0[k Q0 + mq] = w_R^(mq k),  k < E0, mq < Q0;
+//   level j:  Tj[k Q + mq]  = w_S^(mq k),  k < 16, mq < Q = S / 16, with
+//             S = Q0 / 16^(j-1) the sub-problem size, j = 1 .. levels - 2,
+// each level right after the previous one.
+inline int64_t digit_table_entries(int log_r)
+{
+    if (log_r < 4 || log_r > 12) return 0;
+    const int ns = (log_r + 3) / 4;
+    if (ns < 2) return 0;
+    const int l0 = log_r - 4 * (ns - 1);
+    int64_t total = (int64_t)1 << log_r;
+    int64_t S = ((int64_t)1 << log_r) >> l0;
+    for (int j = 1; j <= ns - 2; j++, S /= 16) total += S;
+    return total;
+}
+cudaError_t launch_digit_tables(void *dst, int kind, int log_r, cudaStream_t s);
 // complex128 passes in double-float arithmetic (tiles_df64.cu); only tiles
 // of 2^4..2^12 points with the tile kernel's widths
 bool df64_covers(const PassArgs &a);

@@ -141,6 +141,8 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
         p.tw_m = R * p.B;
         p.tw_tile_off = tables;
         tables += (size_t)R;
+        p.tw_digit_off = tables;
+        tables += (size_t)digit_table_entries(p.log_r);
         if (!last) {
             const int lm = ilog2(p.tw_m);
             p.tw_lo_bits = std::max(1, (lm + 1) / 2);
@@ -186,6 +188,8 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
             return launch_twiddle_f32((float *)(tw + off * eb), count, m, stride, s);
         };
         cudaError_t e = gen(p.tw_tile_off, R, R, 1);
+        if (e == cudaSuccess)
+            e = launch_digit_tables(tw + p.tw_digit_off * eb, dt == FFT_C128 ? 0 : 1, p.log_r, s);
         if (e == cudaSuccess && i < g - 1) {
             e = gen(p.tw_pass_off, (int64_t)1 << p.tw_lo_bits, p.tw_m, 1);
             if (e == cudaSuccess) e = gen(p.tw_hi_off, p.tw_m >> p.tw_lo_bits, p.tw_m, (int64_t)1 << p.tw_lo_bits);
@@ -218,6 +222,7 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
             a.B = p.B;
             a.is_last = (i == g - 1);
             a.tw_tile = tw + p.tw_tile_off * eb;
+            a.tw_digit = tw + p.tw_digit_off * eb;
             a.tw_pass = tw + p.tw_pass_off * eb;
             a.tw_hi = tw + p.tw_hi_off * eb;
             a.tw_lo_bits = p.tw_lo_bits;

@@ -20,6 +20,9 @@
 //   3. For each further radix-16 digit: read 16 points, codelet, weights
 //      w_S^(mq*k) (S the current sub-problem size), write back -- except
 //      after the last digit, whose results stay in registers.
+//      The weights of steps 2 and 3 come from per-level tables with rows by
+//      k (digit_table_entries), so the lanes of a warp, which run over mq,
+//      read consecutive entries.
 //   4. Registers -> HBM: the point with tile index k (natural order) is
 //      multiplied by the weight w_{R*B}^(b*k) the next passes need and
 //      stored in place (non-last pass), or scaled and stored through the
@@ -263,7 +266,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     const int64_t n = p.n;
     (void)NS; (void)G0; (void)Q0; (void)U; (void)E0; (void)n; (void)u;
     using M = MemOf<T>;
-    const V *twt = reinterpret_cast<const V *>(p.tw_tile);
+    const V *twd = reinterpret_cast<const V *>(p.tw_digit);  // weights between digits, rows by k
     typename M::E *out = reinterpret_cast<typename M::E *>(p.out);
     const int64_t sbase = r.sbase, b0 = r.b0, tr = r.tr, vrow = r.vrow;
     const bool valid = r.valid;
@@ -278,7 +281,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             if constexpr (NS > 1) {
                 const int mq = g * U + u;
 #pragma unroll
-                for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twt + mq * k));
+                for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twd + k * Q0 + mq));
             }
         }
     }
@@ -291,6 +294,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + g * U + u) * W + w] = v[g * E0 + k];
         __syncthreads();
         int S = Q0;
+        int doff = R;  // this digit level's table
         // one copy of the radix-16 digit's code for double-float, whose
         // unrolled codelets would overflow the instruction cache
         constexpr int kUnroll = std::is_same<T, dfloat>::value ? 1 : 4;
@@ -304,10 +308,10 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             if (valid) dft_codelet<DIR, 4>(v);
             if (j < NS - 1) {
                 if (valid && mq != 0) {
-                    const int step = R / S;
 #pragma unroll
-                    for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twt + mq * k * step));
+                    for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twd + doff + k * Q + mq));
                 }
+                doff += S;
                 // each thread rewrites exactly the positions it read
 #pragma unroll
                 for (int k = 0; k < 16; k++) tile[tpad(pos0 + k * Q) * W + w] = v[k];

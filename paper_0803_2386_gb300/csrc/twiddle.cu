@@ -109,4 +109,20 @@ cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_digit_tables(void *dst, int kind, int log_r, cudaStream_t s)
+{
+    if (digit_table_entries(log_r) == 0) return cudaSuccess;
+    const size_t eb = kind == 1 ? 8 : 16;
+    const int ns = (log_r + 3) / 4;
+    const int l0 = log_r - 4 * (ns - 1);
+    const int64_t R = (int64_t)1 << log_r, Q0 = R >> l0;
+    cudaError_t e = launch_twiddle_2d(dst, kind, (int64_t)1 << l0, Q0, R, 1, s);
+    int64_t off = R, S = Q0;
+    for (int j = 1; j <= ns - 2 && e == cudaSuccess; j++, S /= 16) {
+        e = launch_twiddle_2d(static_cast<char *>(dst) + off * eb, kind, 16, S / 16, S, 1, s);
+        off += S;
+    }
+    return e;
+}
+
 }  // namespace moafft
