@@ -268,12 +268,28 @@ def test_latency_schedule_for_tiny_batches():
 
 @pytest.mark.parametrize("t", [22, 24])
 def test_large_complex64_three_passes(t):
-    """Large complex64 transforms (2^22: two passes of 2^11, 2^24: three of
-    2^8; pass weights split by the digits of k), every transform against the
-    oracle."""
+    """Large complex64 transforms (2^22: passes of 2^7, 2^7, 2^8; 2^24:
+    three of 2^8; pass weights split by the digits of k), every transform
+    against the oracle."""
     n = 1 << t
     batch = 2
     x = W.uniform_complex(n, batch, seed=60 + t)
     y = run_plan(x, M.FFT_C64)
     ref = O.fft(rounded(x, M.FFT_C64), "forward", c=4096, threads=2)
     assert rel_rows(y, ref).max() <= 1e-6 * t
+
+
+@pytest.mark.parametrize("t,split", [(17, [8, 9]), (18, [8, 10]), (19, [9, 10]), (20, [10, 10]), (21, [7, 7, 7])])
+def test_complex64_default_splits(t, split):
+    """The measured complex64 default splits between 2^16 and 2^22 points,
+    forward and inverse, with an odd batch (a ragged last column group),
+    every transform against the oracle."""
+    n = 1 << t
+    s = json.loads(M.fft_describe_schedule(n, M.FFT_C64))
+    assert [q["log_r"] for q in s["passes"]] == split
+    x = W.uniform_complex(n, 3, seed=80 + t)
+    xr = rounded(x, M.FFT_C64)
+    for direction in (M.FFT_FORWARD, M.FFT_INVERSE):
+        y = run_plan(x, M.FFT_C64, direction)
+        err = rel_rows(y, oracle_op(xr, direction, False))
+        assert err.max() <= tol(M.FFT_C64, n), (t, direction, err.max())
