@@ -202,8 +202,8 @@ static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
     // complex64 passes are HBM-bound, and the narrow column tiles of radices
     // above 2^10 (width 2 or 1) waste DRAM sectors: a third pass of <= 2^10
     // points costs less than one such pass.  The splits are the fastest of
-    // an exhaustive sweep of two- and three-pass schedules on GB300 (1 GiB
-    // batches), the smaller radix first where the order mattered.
+    // a sweep on GB300 (1 GiB batches) of every two-pass schedule and the
+    // three-pass ones whose neighbouring radices differ by at most 2.
     static const char *const c64_split[] = {
         "7,6",   "7,7",    "7,8",    "8,8",   "8,9",   "8,10",  // 2^13 .. 2^18
         "9,10",  "10,10",  "7,7,7",  "7,7,8", "7,8,8", "8,8,8"  // 2^19 .. 2^24
