@@ -491,13 +491,30 @@ def extra_configs(M, torch, dev, stream):
     y = torch.empty_like(x)
     p = M.Plan(n, 1, M.FFT_C128, M.FFT_FORWARD)
     ms = _time(torch, stream, lambda: p.exec(x, y, stream), 200)
-    M.fft_plan_profile(p.handle, True)
-    for _ in range(50):
-        p.exec(x, y, stream)
-    kt = M.fft_plan_pass_times(p.handle)
-    kms = sum(t for t, _ in kt) / 50
-    _emit({"config": "c128 n=2^10 batch 1 forward", "us_per_call_host_bound": round(ms * 1e3, 3),
-           "us_kernel": round(kms * 1e3, 3), "gflops_kernel": round(5 * n * 10 / (kms * 1e-3) / 1e9, 3)})
+    # device time per call without the host: 50 calls captured in one CUDA
+    # graph, replayed between events
+    # (graphs are captured on a side stream)
+    graph = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream(device=dev)
+    cs.wait_stream(torch.cuda.current_stream(dev))
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(graph, stream=cs):
+            for _ in range(50):
+                p.exec(x, y, cs)
+        graph.replay()
+        cs.synchronize()
+        e0.record(cs)
+        graph.replay()
+        e1.record(cs)
+        cs.synchronize()
+    kms = e0.elapsed_time(e1) / 50
+    ref = torch.fft.fft(x.to(torch.complex128))
+    _emit({"config": "c128 n=2^10 batch 1 forward", "schedule": [q["log_r"] for q in json.loads(p.describe())["schedule"]["passes"]],
+           "us_per_call_host_bound": round(ms * 1e3, 3),
+           "us_per_call_device": round(kms * 1e3, 3), "gflops_device": round(5 * n * 10 / (kms * 1e-3) / 1e9, 3),
+           "rel_err_vs_torch_fft": rel(y, ref)})
     p.close()
 
     # precision forms: complex64 n = 2^16, batch 4096 (Gaussian sigma = 1)

@@ -789,13 +789,23 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
     st = build_schedule(c.sched, n, dt, schedule, &req_chunk);
     if (st == FFT_OK && c.sched.cluster && form != FFT_FORM_PLAIN)
         st = fail(FFT_ERR_UNSUPPORTED, "schedule 'cluster' runs the plain complex64 form only");
-    // latency: a few small transforms fill few thread blocks, and a tile of
-    // W rows computes W-1 idle rows.  Two passes one column / row wide spread
-    // the same work over R times more blocks (measured on one complex128
-    // transform: n = 2^10 41 -> 21 us, n = 2^14 66 -> 33 us).
+    // latency (complex128): a few small transforms fill few thread blocks,
+    // each bound by its SM's FP64 issue rate, and a tile of W rows computes
+    // W-1 idle rows.  Two passes of narrow tiles spread the same work over
+    // more blocks: the width is the smallest power of two that leaves at most
+    // 512 tiles in the first pass (measured, in graph replays: n = 2^10
+    // batch 1 40 -> 17 us, batch 32 43 -> 21 us; n = 2^12 batch 8 50 -> 23
+    // us; n = 2^14 batch 1 62 -> 28 us).  Complex64 tiles are not
+    // issue-bound at these sizes and keep the default (a single pass at
+    // n = 2^10: 4.3 us against 7.2 us for two narrow passes).
     const int t = exact_log2(n);
-    if (st == FFT_OK && chosen.empty() && form == FFT_FORM_PLAIN && n * batch <= ((int64_t)1 << 15) && t >= 6) {
-        const std::string lat = std::to_string((t + 1) / 2) + "@1," + std::to_string(t / 2) + "@1";
+    if (st == FFT_OK && chosen.empty() && form == FFT_FORM_PLAIN && dt == FFT_C128 &&
+        n * batch <= ((int64_t)1 << 15) && t >= 6) {
+        const int64_t tiles = batch << (t / 2);  // first pass: batch * B columns
+        int w = 1;
+        while (w < 32 && tiles > 512 * (int64_t)w) w *= 2;
+        const std::string lat = std::to_string((t + 1) / 2) + "@" + std::to_string(w) + "," +
+                                std::to_string(t / 2) + "@" + std::to_string(w);
         st = build_schedule(c.sched, n, dt, lat.c_str(), &req_chunk);
     }
     if (st == FFT_OK && form == FFT_FORM_DF64) {

@@ -248,22 +248,29 @@ def test_unblocked_stages(dt, t, order):
     assert rel_rows(y, oracle_op(xr, M.FFT_FORWARD, False)).max() <= tol(dt, n)
 
 
+def plan_passes(n, batch, dt):
+    p = M.fft_plan(n, batch, dt, M.FFT_FORWARD)
+    try:
+        s = json.loads(M.fft_plan_describe(p))["schedule"]
+    finally:
+        M.fft_destroy(p)
+    return [(q["log_r"], q["width"]) for q in s["passes"]]
+
+
 def test_latency_schedule_for_tiny_batches():
-    """A few small transforms take two passes one column / row wide (many
-    thread blocks instead of one tile with idle rows); larger batches keep the
-    tile passes."""
-    p = M.fft_plan(1 << 10, 1, M.FFT_C128, M.FFT_FORWARD)
-    try:
-        s = json.loads(M.fft_plan_describe(p))["schedule"]
-    finally:
-        M.fft_destroy(p)
-    assert [q["log_r"] for q in s["passes"]] == [5, 5] and [q["width"] for q in s["passes"]] == [1, 1]
-    p = M.fft_plan(1 << 10, 64, M.FFT_C128, M.FFT_FORWARD)
-    try:
-        s = json.loads(M.fft_plan_describe(p))["schedule"]
-    finally:
-        M.fft_destroy(p)
-    assert [q["log_r"] for q in s["passes"]] == [10]
+    """A few small complex128 transforms take two passes of narrow tiles
+    (many thread blocks instead of one tile with idle rows; at most 512 tiles
+    in the first pass); larger batches and complex64 keep the tile passes."""
+    assert plan_passes(1 << 10, 1, M.FFT_C128) == [(5, 1), (5, 1)]
+    assert plan_passes(1 << 10, 32, M.FFT_C128) == [(5, 2), (5, 2)]
+    assert plan_passes(1 << 6, 512, M.FFT_C128) == [(3, 8), (3, 8)]
+    assert plan_passes(1 << 10, 64, M.FFT_C128) == [(10, 4)]
+    assert plan_passes(1 << 10, 1, M.FFT_C64) == [(10, 4)]
+    for n, batch in ((1 << 10, 32), (1 << 6, 512), (1 << 13, 3)):
+        x = W.uniform_complex(n, batch, seed=5)
+        for direction in (M.FFT_FORWARD, M.FFT_INVERSE):
+            y = run_plan(x, M.FFT_C128, direction)
+            assert rel_rows(y, oracle_op(x, direction, False)).max() <= 1e-12
 
 
 @pytest.mark.parametrize("t", [22, 24])
