@@ -669,6 +669,32 @@ def extra_configs(M, torch, dev, stream):
            "gbs": round(4 * n * batch * 8 / (ms * 1e-3) / 1e9, 1)})
     pd.close()
 
+    # multi-dimensional transforms (the last axis as 1-D transforms, each
+    # other axis one column pass); error against the complex128 plan on the
+    # same input (the parity tests check that one against the oracle)
+    for dims, batch, f64 in (((4096, 4096), 8, False), ((256, 256, 256), 8, False),
+                             ((2048, 2048), 16, True), ((128, 128, 128), 32, True)):
+        npts = math.prod(dims)
+        tdt = torch.complex128 if f64 else torch.complex64
+        gen = torch.Generator(device=dev).manual_seed(len(dims))
+        x = torch.randn((batch,) + dims, dtype=tdt, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        pn = M.PlanND(dims, batch, M.FFT_C128 if f64 else M.FFT_C64, M.FFT_FORWARD)
+        ms = _time(torch, stream, lambda: pn.exec(x, y, stream), 5)
+        row = {"config": f"{'c128' if f64 else 'c64'} {len(dims)}-D {'x'.join(map(str, dims))} batch {batch} forward",
+               "ms": round(ms, 3), "launches": pn.launches,
+               "gflops": round(5.0 * npts * math.log2(npts) * batch / (ms * 1e-3) / 1e9, 1),
+               "gbs_one_round_trip": round(2 * npts * batch * (16 if f64 else 8) / (ms * 1e-3) / 1e9, 1)}
+        if not f64:
+            xr = x[:1].to(torch.complex128)
+            yr = torch.empty_like(xr)
+            with M.PlanND(dims, 1, M.FFT_C128, M.FFT_FORWARD) as pr:
+                pr.exec(xr, yr, stream)
+            row["rel_err_vs_fp64"] = rel(y[:1], yr)
+        _emit(row)
+        pn.close()
+        del x, y
+
     # radix sweep at n = 2^24 (the paper's Table 4 sweeps the radix of
     # fftpsiradn at 2^24): three passes of 2^8 through the generic tile kernel
     # (width 8 keeps every variant on the same kernel), register digits of

@@ -13,6 +13,8 @@ binary64, no fused multiply-add).  What each one follows in the paper
   (Fig. vanloan_fft: "Output: the FFT of x"), brute force in long double.
 * :func:`fftpsirad2` -- Fig. fftpsirad2 / rad2_fft, preceded by the
   bit-reversal P_n of Fig. vanloan_fft line (1).
+* :func:`fftn` -- multi-dimensional transforms as 1-D transforms along
+  every axis (Sec. "Conclusions for the General Radix Approach", footnote).
 * :func:`moa_fft` -- the cache-optimised algorithm of Ch.3 (Sec. butter-order
   steps (1)-(5)): stages inside rows of length c, reshape-transposes
   (Eqs. reshape1-3, xdeqn), weights carried like the data (Eqs. xi1, xi2),
@@ -238,6 +240,21 @@ def fft(x, op: str = "forward", c: int = 1024, threads: int = 1) -> np.ndarray:
     _check(lib().oracle_fft_many(_fp(x), _fp(y), n, batch, _OPS[op], int(c), int(threads)),
            "oracle_fft_many")
     return y
+
+
+def fftn(x, ndim: int | None = None, op: str = "forward", c: int = 1024, threads: int = 1) -> np.ndarray:
+    """Multi-dimensional transform of the last `ndim` axes (default: all):
+    the multi-dimensional DFT kernel is a product of one 1-D kernel per
+    axis, so it is the 1-D transform (:func:`fft`, same `op`) applied along
+    each axis in turn, as the paper builds multi-dimensional FFTs from its
+    1-D one (Sec. "Conclusions for the General Radix Approach").  An inverse
+    is scaled by 1/n_i on every axis, 1/prod(n_i) in all."""
+    y = _c128(x)
+    ndim = y.ndim if ndim is None else ndim
+    for axis in range(y.ndim - ndim, y.ndim):
+        moved = np.ascontiguousarray(np.moveaxis(y, axis, -1))
+        y = np.moveaxis(fft(moved, op, c=c, threads=threads), -1, axis)
+    return np.ascontiguousarray(y)
 
 
 def library_path() -> str:

@@ -15,6 +15,7 @@ hand-written adjoint.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
@@ -39,7 +40,7 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
                 -7: "FFT_ERR_TIMEOUT", -8: "FFT_ERR_UNSUPPORTED"}
 
 # every symbol include/moafft.h declares
-EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_exec", "fft_exec_adjoint",
+EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_plan_nd", "fft_exec", "fft_exec_adjoint",
            "fft_exec_host", "fft_exec_noalloc", "fft_plan_check", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
            "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_tune_candidates", "fft_version",
            "dm_gate", "dm_transpose_vector"]
@@ -76,6 +77,7 @@ def lib():
             "fft_plan": (i32, [ctypes.POINTER(vp), i64, i64, i32, i32]),
             "fft_plan_ex": (i32, [ctypes.POINTER(vp), i64, i64, i32, i32, i32, ctypes.c_char_p]),
             "fft_plan_many": (i32, [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i32, i32]),
+            "fft_plan_nd": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), i64, i32, i32]),
             "fft_exec": (i32, [vp, vp, vp, vp]),
             "fft_exec_adjoint": (i32, [vp, vp, vp, vp]),
             "fft_exec_host": (i32, [vp, vp, vp, vp]),
@@ -160,6 +162,15 @@ def fft_plan_many(sizes, dtype: int = FFT_C64, direction: int = FFT_FORWARD) -> 
     arr = (ctypes.c_int64 * max(1, len(sizes)))(*sizes)
     h = ctypes.c_void_p()
     _check(lib().fft_plan_many(ctypes.byref(h), arr, len(sizes), dtype, direction))
+    return h.value
+
+
+def fft_plan_nd(dims, batch: int = 1, dtype: int = FFT_C128, direction: int = FFT_FORWARD) -> int:
+    """Plan over arrays of shape dims (row-major, last axis contiguous)."""
+    dims = [int(d) for d in dims]
+    arr = (ctypes.c_int64 * max(1, len(dims)))(*dims)
+    h = ctypes.c_void_p()
+    _check(lib().fft_plan_nd(ctypes.byref(h), len(dims), arr, batch, dtype, direction))
     return h.value
 
 
@@ -370,6 +381,38 @@ def fft(x, inverse: bool = False, form: int = FFT_FORM_PLAIN, schedule: str | No
 
 def ifft(x, form: int = FFT_FORM_PLAIN, schedule: str | None = None):
     return fft(x, inverse=True, form=form, schedule=schedule)
+
+
+class PlanND(Plan):
+    """Owning wrapper of a multi-dimensional plan (fft_plan_nd)."""
+
+    def __init__(self, dims, batch: int = 1, dtype: int = FFT_C128, direction: int = FFT_FORWARD):
+        self.dims = tuple(int(d) for d in dims)
+        self.n = math.prod(self.dims)
+        self.batch, self.dtype, self.direction, self.form = batch, dtype, direction, FFT_FORM_PLAIN
+        self.handle = fft_plan_nd(self.dims, batch, dtype, direction)
+
+
+def fftn(x, ndim: int | None = None, inverse: bool = False):
+    """Transform the last `ndim` axes (default: all) of a contiguous complex
+    CUDA tensor; the leading axes are the batch."""
+    import torch
+    x = x.contiguous()
+    ndim = x.dim() if ndim is None else ndim
+    dims = tuple(x.shape[x.dim() - ndim:])
+    batch = x.numel() // max(math.prod(dims), 1)
+    key = ("nd", dims, batch, _dtype_code(x), inverse, torch.cuda.current_device())
+    p = _PLAN_CACHE.get(key)
+    if p is None:
+        p = PlanND(dims, batch, _dtype_code(x), FFT_INVERSE if inverse else FFT_FORWARD)
+        _PLAN_CACHE[key] = p
+    out = torch.empty_like(x)
+    p.exec(x, out)
+    return out
+
+
+def ifftn(x, ndim: int | None = None):
+    return fftn(x, ndim, inverse=True)
 
 
 def _make_autograd():

@@ -457,6 +457,17 @@ struct SizeClass {
     bool off_even = true;        // every offset a multiple of 2 points
     int64_t off_align = 1024;    // largest power of two (<= 1024) dividing every offset
     DevBuf d_off;                // the same on the device
+    double inv_scale = 0.0;      // inverse scaling in the last pass (0: 1/n)
+};
+
+// One axis (other than the last) of a multi-dimensional plan: one column
+// pass in place on the output, or two (the axis's 1-D schedule r0, r1 laid
+// over its strided lines) from the output to the workspace and back, in
+// rounds of `chunk` arrays.
+struct AxisPlan {
+    int npass = 1;
+    PassDesc pass[2];
+    int64_t chunk = 1;
 };
 
 struct fft_plan_s {
@@ -507,7 +518,19 @@ struct fft_plan_s {
     // on the same buffers skip the cudaPointerGetAttributes round trips
     const void *ok_in = nullptr;
     const void *ok_out = nullptr;
+    // multi-dimensional plans (fft_plan_nd): the shape, and after classes[0]
+    // (the last axis) the passes of every other axis, with their own tables
+    std::vector<int64_t> dims;
+    std::vector<AxisPlan> axes;
+    DevBuf tw_axes;
 };
+
+// the inverse transform's scaling, applied in a class's last pass
+static double class_scale(const fft_plan_s *p, const SizeClass &C)
+{
+    if (p->dir != FFT_INVERSE) return 1.0;
+    return C.inv_scale > 0.0 ? C.inv_scale : 1.0 / (double)C.n;
+}
 
 static cudaEvent_t take_event(fft_plan_s *p)
 {
@@ -551,13 +574,69 @@ static int64_t launches_per_exec(const fft_plan_s *p)
 {
     if (p->persist) return 1;
     int64_t k = 0;
+    for (const auto &ax : p->axes) k += ax.npass == 1 ? 1 : 2 * ((p->batch + ax.chunk - 1) / ax.chunk);
     for (const auto &c : p->classes) k += class_launches(c);
     return k;
 }
 
+// Offsets (in table entries) of one pass's weight tables: the tile table
+// (R entries), the digit tables, and for passes with pass weights their
+// table(s), whose rows hold B >> col_shift columns.
+static void layout_pass_tables(PassDesc &d, bool last, size_t &off)
+{
+    d.tw_tile_off = off;
+    off += (size_t)1 << d.log_r;
+    d.tw_digit_off = off;
+    off += (size_t)digit_table_entries(d.log_r);
+    if (last || d.tw_mode == kTwNone) return;
+    const int64_t cols = d.B >> d.col_shift;
+    d.tw_pass_off = off;
+    if (d.tw_mode == 3) {
+        off += (size_t)(((int64_t)1 << (d.log_r - 4)) * cols);
+        d.tw_hi_off = off;
+        off += (size_t)(16 * cols);
+    } else if (d.tw_mode == 2) {
+        off += (size_t)(((int64_t)1 << d.log_r) * cols);
+    } else if (d.tw_lo_bits == 0) {
+        off += (size_t)d.tw_m;
+    } else {
+        off += (size_t)1 << d.tw_lo_bits;
+        d.tw_hi_off = off;
+        off += (size_t)(d.tw_m >> d.tw_lo_bits);
+    }
+}
+
+// Fill the tables layout_pass_tables placed in `arena`.
+static cudaError_t gen_pass_tables(const fft_plan_s *p, char *arena, const PassDesc &d, bool last)
+{
+    const size_t wb = p->form == FFT_FORM_DF64 ? 16 : elem_bytes(p->dt);
+    const int kind = p->form == FFT_FORM_DF64 ? 2 : (p->dt == FFT_C128 ? 0 : 1);
+    auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
+        if (p->form == FFT_FORM_DF64) return launch_twiddle_df64((float *)(arena + o * wb), count, m, stride, 0);
+        if (p->dt == FFT_C128) return launch_twiddle_f64((double *)(arena + o * wb), count, m, stride, 0);
+        return launch_twiddle_f32((float *)(arena + o * wb), count, m, stride, 0);
+    };
+    const int64_t R = (int64_t)1 << d.log_r;
+    cudaError_t e = gen(d.tw_tile_off, R, R, 1);
+    if (e == cudaSuccess) e = launch_digit_tables(arena + d.tw_digit_off * wb, kind, d.log_r, 0);
+    if (e != cudaSuccess || last || d.tw_mode == kTwNone) return e;
+    const int64_t cols = d.B >> d.col_shift;
+    if (d.tw_mode == 2) return launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, R, cols, d.tw_m, 1, 0);
+    if (d.tw_mode == 3) {
+        const int64_t U = (int64_t)1 << (d.log_r - 4);
+        e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, U, cols, d.tw_m, 1, 0);
+        if (e == cudaSuccess) e = launch_twiddle_2d(arena + d.tw_hi_off * wb, kind, 16, cols, d.tw_m, U, 0);
+        return e;
+    }
+    if (d.tw_lo_bits == 0) return gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
+    e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
+    if (e == cudaSuccess) e = gen(d.tw_hi_off, d.tw_m >> d.tw_lo_bits, d.tw_m, (int64_t)1 << d.tw_lo_bits);
+    return e;
+}
+
 static int make_tables(fft_plan_s *p)
 {
-    // arena layout: per class, per pass, the tile table (R entries) and the
+    // arena layout: per class, per pass, the tile and digit tables and the
     // pass table(s)
     size_t eb = elem_bytes(p->dt);
     size_t off = 0;
@@ -570,27 +649,7 @@ static int make_tables(fft_plan_s *p)
             c.sched.tw_direct_off = off;
             off += (size_t)c.n;
         }
-        for (int i = 0; i < c.sched.npass; i++) {
-            PassDesc &d = c.sched.pass[i];
-            d.tw_tile_off = off;
-            off += (size_t)1 << d.log_r;
-            d.tw_digit_off = off;
-            off += (size_t)digit_table_entries(d.log_r);
-            if (i < c.sched.npass - 1) {
-                d.tw_pass_off = off;
-                if (d.tw_mode == 3) {
-                    off += (size_t)(((int64_t)1 << (d.log_r - 4)) * d.B);
-                    d.tw_hi_off = off;
-                    off += (size_t)(16 * d.B);
-                } else if (d.tw_lo_bits == 0) {
-                    off += (size_t)d.tw_m;
-                } else {
-                    off += (size_t)1 << d.tw_lo_bits;
-                    d.tw_hi_off = off;
-                    off += (size_t)(d.tw_m >> d.tw_lo_bits);
-                }
-            }
-        }
+        for (int i = 0; i < c.sched.npass; i++) layout_pass_tables(c.sched.pass[i], i == c.sched.npass - 1, off);
     }
     int st = dev_alloc(p->tw, off * eb, "twiddle tables");
     if (st != FFT_OK) return st;
@@ -608,34 +667,7 @@ static int make_tables(fft_plan_s *p)
             if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
         }
         for (int i = 0; i < c.sched.npass; i++) {
-            PassDesc &d = c.sched.pass[i];
-            int64_t R = (int64_t)1 << d.log_r;
-            auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
-                if (p->form == FFT_FORM_DF64)
-                    return launch_twiddle_df64((float *)p->tw.ptr + 4 * o, count, m, stride, 0);
-                if (p->dt == FFT_C128)
-                    return launch_twiddle_f64((double *)p->tw.ptr + 2 * o, count, m, stride, 0);
-                return launch_twiddle_f32((float *)p->tw.ptr + 2 * o, count, m, stride, 0);
-            };
-            const int kind = p->form == FFT_FORM_DF64 ? 2 : (p->dt == FFT_C128 ? 0 : 1);
-            const size_t wb = p->form == FFT_FORM_DF64 ? 16 : eb;
-            char *arena = (char *)p->tw.ptr;
-            cudaError_t e = gen(d.tw_tile_off, R, R, 1);
-            if (e == cudaSuccess) e = launch_digit_tables(arena + d.tw_digit_off * wb, kind, d.log_r, 0);
-            if (e == cudaSuccess && i < c.sched.npass - 1) {
-                if (d.tw_mode == 2) {
-                    e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, R, d.B, d.tw_m, 1, 0);
-                } else if (d.tw_mode == 3) {
-                    const int64_t U = (int64_t)1 << (d.log_r - 4);
-                    e = launch_twiddle_2d(arena + d.tw_pass_off * wb, kind, U, d.B, d.tw_m, 1, 0);
-                    if (e == cudaSuccess) e = launch_twiddle_2d(arena + d.tw_hi_off * wb, kind, 16, d.B, d.tw_m, U, 0);
-                } else if (d.tw_lo_bits == 0) e = gen(d.tw_pass_off, d.tw_m, d.tw_m, 1);
-                else {
-                    e = gen(d.tw_pass_off, (int64_t)1 << d.tw_lo_bits, d.tw_m, 1);
-                    if (e == cudaSuccess)
-                        e = gen(d.tw_hi_off, d.tw_m >> d.tw_lo_bits, d.tw_m, (int64_t)1 << d.tw_lo_bits);
-                }
-            }
+            cudaError_t e = gen_pass_tables(p, (char *)p->tw.ptr, c.sched.pass[i], i == c.sched.npass - 1);
             if (e != cudaSuccess) return fail_cuda(e, "twiddle generation");
         }
     }
@@ -658,6 +690,7 @@ static void destroy_plan(fft_plan_s *p)
 {
     dev_free(p->ws);
     dev_free(p->tw);
+    dev_free(p->tw_axes);
     dev_free(p->err);
     dev_free(p->tcf);
     dev_free(p->d_segs);
@@ -833,6 +866,130 @@ extern "C" int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt,
     return fft_plan_ex(out, n, batch, dt, dir, FFT_FORM_PLAIN, nullptr);
 }
 
+// Multi-dimensional transforms built from the 1-D path (the paper notes
+// that they can be, Sec. "Conclusions for the General Radix Approach"):
+// the last, contiguous axis is a batch of 1-D transforms (classes[0], any
+// length the 1-D plans take); every other axis runs over the arrays viewed
+// as A x L x S (A the product of the axes before it, S of those after it),
+// each column of L points a line of the axis:
+//   * one column pass of radix L whose W-column tiles are whole transforms
+//     of W lines (no pass weights, natural order out, in place), when its
+//     tile rows are at least 128 bytes wide or L < 2^8;
+//   * else the axis's two-pass 1-D schedule r0, r1 laid over the lines:
+//     pass 0 as A x R0 x (R1 S) with the weights w_L^(b k) of column b =
+//     b' >> log2 S, pass 1 as (A R0) x R1 x S storing through the axis's
+//     final transpose, via the workspace.
+// Axes of length 1 drop out.
+extern "C" int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64_t batch, fft_dtype dt,
+                           fft_dir dir)
+{
+    if (!out) return fail(FFT_ERR_ARG, "fft_plan_nd: out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(FFT_ERR_ARG, "fft_plan_nd: dims is NULL");
+    if (ndim < 1 || ndim > kMaxDims) return fail(FFT_ERR_ARG, "fft_plan_nd: ndim = %d outside 1..%d", ndim, kMaxDims);
+    if (batch < 1) return fail(FFT_ERR_ARG, "batch = %lld < 1", (long long)batch);
+    std::vector<int64_t> d;
+    int tsum = 0;
+    for (int i = 0; i < ndim; i++) {
+        int st = check_common(dims[i], dt, dir);
+        if (st != FFT_OK) return st;
+        if (dims[i] > 1) d.push_back(dims[i]);
+        tsum += exact_log2(dims[i]);
+    }
+    if (tsum > 36) return fail(FFT_ERR_UNSUPPORTED, "fft_plan_nd: 2^%d points per array exceeds 2^36", tsum);
+    for (size_t i = 0; i + 1 < d.size(); i++)
+        if (d[i] > ((int64_t)1 << 24))
+            return fail(FFT_ERR_UNSUPPORTED,
+                        "fft_plan_nd: an axis of %lld points before the last; those axes take at most 2^24",
+                        (long long)d[i]);
+    const int64_t per = (int64_t)1 << tsum;
+    const int64_t last = d.empty() ? 1 : d.back();
+    fft_plan_t p = nullptr;
+    int st = fft_plan_ex(&p, last, batch * (per / last), dt, dir, FFT_FORM_PLAIN, nullptr);
+    if (st != FFT_OK) return st;
+    p->n = per;
+    p->batch = batch;
+    p->dims.assign(dims, dims + ndim);
+    p->classes[0].inv_scale = 1.0 / (double)per;
+    const size_t eb = elem_bytes(dt);
+    auto width_for = [&](int log_r, int64_t B) -> int {
+        const int64_t w = (log_r >= 4 && log_r <= 12) ? std::min(32, std::max(1, 4096 >> log_r))
+                                                     : std::min<int64_t>(16, tile_budget(dt) >> log_r);
+        return (int)std::max<int64_t>(1, std::min(w, B));
+    };
+    // rounds of two-pass axes: as the 1-D plans (256 MiB complex128, 2 GiB
+    // complex64 of arrays per workspace round)
+    const int64_t target = dt == FFT_C128 ? ((int64_t)256 << 20) : ((int64_t)2048 << 20);
+    int64_t ws_need = 0;
+    size_t off = 0;
+    int64_t A = 1;
+    for (size_t i = 0; st == FFT_OK && i + 1 < d.size(); i++) {
+        AxisPlan ax;
+        const int lg = exact_log2(d[i]);
+        const int64_t S = per / (A * d[i]);
+        const int64_t wt = (lg >= 4 && lg <= 12) ? std::min(32, std::max(1, 4096 >> lg)) : 16;
+        if (lg < 8 || (lg <= 12 && wt * (int64_t)eb >= 128)) {
+            PassDesc &q = ax.pass[0];
+            q.log_r = lg;
+            q.A = A;
+            q.B = S;
+            q.width = width_for(lg, S);
+            q.max_digit = 4;
+            split_subpasses(q);
+            q.tw_mode = kTwNone;
+            q.tw_m = 1;
+            layout_pass_tables(q, false, off);
+        } else {
+            Schedule s1;
+            const std::string two = std::to_string((lg + 1) / 2) + "," + std::to_string(lg / 2);
+            st = build_schedule(s1, d[i], dt, two.c_str(), nullptr);
+            if (st != FFT_OK) break;
+            ax.npass = 2;
+            const int64_t R0 = (int64_t)1 << s1.pass[0].log_r;
+            ax.pass[0] = s1.pass[0];
+            ax.pass[0].A = A;
+            ax.pass[0].B = s1.pass[0].B * S;
+            ax.pass[0].col_shift = exact_log2(S);
+            // every lane of a warp reads the same weight column b (W <= S):
+            // the digit split keeps the two small tables in L1, where the
+            // whole-table rows of mode 2 (measured: 32 KB at L = 2^12) missed
+            // and left the pass latency-bound
+            ax.pass[0].tw_mode = 3;
+            ax.pass[0].width = width_for(s1.pass[0].log_r, ax.pass[0].B);
+            ax.pass[1] = s1.pass[1];
+            ax.pass[1].A = A * R0;
+            ax.pass[1].B = S;
+            ax.pass[1].col_prev = R0;
+            ax.pass[1].tw_mode = kTwNone;
+            ax.pass[1].width = width_for(s1.pass[1].log_r, S);
+            layout_pass_tables(ax.pass[0], false, off);
+            layout_pass_tables(ax.pass[1], false, off);
+            ax.chunk = std::max<int64_t>(1, std::min<int64_t>(batch, target / (per * (int64_t)eb)));
+            ws_need = std::max<int64_t>(ws_need, ax.chunk * per * (int64_t)eb);
+        }
+        A *= d[i];
+        p->axes.push_back(ax);
+    }
+    if (st == FFT_OK && ws_need > p->ws_bytes) {
+        dev_free(p->ws);
+        st = dev_alloc(p->ws, (size_t)ws_need, "workspace");
+        if (st == FFT_OK) p->ws_bytes = ws_need;
+    }
+    if (st == FFT_OK && !p->axes.empty()) st = dev_alloc(p->tw_axes, off * eb, "axis weight tables");
+    for (size_t i = 0; st == FFT_OK && i < p->axes.size(); i++)
+        for (int k = 0; st == FFT_OK && k < p->axes[i].npass; k++) {
+            cudaError_t e = gen_pass_tables(p, (char *)p->tw_axes.ptr, p->axes[i].pass[k], false);
+            if (e == cudaSuccess && k == p->axes[i].npass - 1) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) st = fail_cuda(e, "axis weight tables");
+        }
+    if (st != FFT_OK) {
+        destroy_plan(p);
+        return st;
+    }
+    *out = p;
+    return FFT_OK;
+}
+
 // tiles a pass launches for `count` transforms at width W
 static int64_t pass_ctas(const PassDesc &d, int64_t count)
 {
@@ -906,7 +1063,7 @@ static void fill_args(const fft_plan_s *p, const SizeClass &C, int i, PassArgs &
     a.tw_hi = (const char *)p->tw.ptr + d.tw_hi_off * eb;
     a.tw_lo_bits = d.tw_lo_bits;
     a.tw_mode = d.tw_mode;
-    a.scale = a.is_last && p->dir == FFT_INVERSE ? 1.0 / (double)C.n : 1.0;
+    a.scale = a.is_last ? class_scale(p, C) : 1.0;
     a.err = (int *)p->err.ptr;
 }
 
@@ -1068,7 +1225,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
 {
     size_t eb = elem_bytes(p->dt);
     const Schedule &S = C.sched;
-    const double scale = (p->dir == FFT_INVERSE) ? 1.0 / (double)C.n : 1.0;
+    const double scale = class_scale(p, C);
     const bool ragged = C.d_off.ptr != nullptr;
     if (S.unblocked) {
         if (ragged) return fail(FFT_ERR_UNSUPPORTED, "the per-stage schedule takes dense batches");
@@ -1161,13 +1318,83 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
     return FFT_OK;
 }
 
+// The passes of a multi-dimensional plan's other axes.  Pass d works on the
+// arrays viewed as A x R x B (the axis's lines run with stride B); a
+// one-pass axis runs in place on out, a two-pass axis goes out -> workspace
+// -> out per round of arrays.
+static int launch_axis_pass(fft_plan_t p, const PassDesc &d, const void *in, void *out, int64_t count,
+                            int pass_index, int sign, cudaStream_t s)
+{
+    const size_t eb = elem_bytes(p->dt);
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.in = in;
+    a.out = out;
+    a.n = p->n;
+    a.count = count;
+    a.npass = 1;
+    a.pass_log[0] = d.log_r;
+    a.log_r = d.log_r;
+    a.width = d.width;
+    a.nsub = d.nsub;
+    for (int k = 0; k < kMaxSub; k++) a.sub_log[k] = d.sub_log[k];
+    a.A = d.A;
+    a.B = d.B;
+    a.is_last = 0;
+    a.tw_tile = (const char *)p->tw_axes.ptr + d.tw_tile_off * eb;
+    a.tw_digit = (const char *)p->tw_axes.ptr + d.tw_digit_off * eb;
+    a.tw_pass = (const char *)p->tw_axes.ptr + d.tw_pass_off * eb;
+    a.tw_hi = (const char *)p->tw_axes.ptr + d.tw_hi_off * eb;
+    a.tw_lo_bits = d.tw_lo_bits;
+    a.tw_mode = d.tw_mode;
+    a.col_shift = d.col_shift;
+    a.col_prev = d.col_prev;
+    a.scale = 1.0;
+    a.err = (int *)p->err.ptr;
+    fft_plan_s::Rec rec{pass_index, nullptr, nullptr};
+    if (p->profile) {
+        rec.a = take_event(p);
+        rec.b = take_event(p);
+        if (rec.a) cudaEventRecord(rec.a, s);
+    }
+    const cudaError_t e = p->dt == FFT_C128 ? launch_pass_f64(a, sign, s) : launch_pass_f32(a, sign, s);
+    if (e != cudaSuccess) return fail_cuda(e, "axis pass launch");
+    if (p->profile && rec.a && rec.b) {
+        cudaEventRecord(rec.b, s);
+        p->recs.push_back(rec);
+    }
+    return FFT_OK;
+}
+
+static int exec_axes(fft_plan_t p, void *out, int sign, cudaStream_t s)
+{
+    const size_t eb = elem_bytes(p->dt);
+    int idx = p->classes.empty() ? 0 : p->classes[0].sched.npass;
+    for (const auto &ax : p->axes) {
+        int st = FFT_OK;
+        if (ax.npass == 1) {
+            st = launch_axis_pass(p, ax.pass[0], out, out, p->batch, idx, sign, s);
+        } else {
+            for (int64_t c0 = 0; c0 < p->batch && st == FFT_OK; c0 += ax.chunk) {
+                const int64_t c = std::min(ax.chunk, p->batch - c0);
+                char *arr = (char *)out + (size_t)c0 * p->n * eb;
+                st = launch_axis_pass(p, ax.pass[0], arr, p->ws.ptr, c, idx, sign, s);
+                if (st == FFT_OK) st = launch_axis_pass(p, ax.pass[1], p->ws.ptr, arr, c, idx + 1, sign, s);
+            }
+        }
+        if (st != FFT_OK) return st;
+        idx += ax.npass;
+    }
+    return FFT_OK;
+}
+
 static int exec_all(fft_plan_t p, const void *in, void *out, int sign, cudaStream_t s)
 {
     for (const auto &c : p->classes) {
         int st = exec_class(p, c, in, out, 0, c.count, sign, s);
         if (st != FFT_OK) return st;
     }
-    return FFT_OK;
+    return exec_axes(p, out, sign, s);
 }
 
 // Uneven plans: capture the whole launch sequence once per (in, out, sign)
@@ -1332,8 +1559,9 @@ static int setup_staging(fft_plan_t p)
 static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
 {
     if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
-    if (p->classes.size() != 1 || p->n == 0)
-        return fail(FFT_ERR_UNSUPPORTED, "fft_exec_host takes plans of one length (fft_plan / fft_plan_ex)");
+    if (p->classes.size() != 1 || p->n == 0 || !p->dims.empty())
+        return fail(FFT_ERR_UNSUPPORTED,
+                    "fft_exec_host takes one-dimensional plans of one length (fft_plan / fft_plan_ex)");
     int st = check_host_ptr(in, "in");
     if (st == FFT_OK) st = check_host_ptr(out, "out");
     if (st == FFT_OK) st = setup_staging(p);
@@ -1443,6 +1671,7 @@ extern "C" int fft_plan_pass_times(fft_plan_t p, double *ms, int64_t *launches, 
     p->recs.clear();
     int np = 0;
     for (const auto &c : p->classes) np = std::max(np, c.sched.npass);
+    for (const auto &ax : p->axes) np += ax.npass;
     return p->use_graph ? 1 : np;
 }
 
@@ -1550,6 +1779,23 @@ extern "C" int fft_plan_describe(fft_plan_t p, char *buf, int64_t len)
         if (p->classes[0].sched.cluster)
             j += ", \"resident_clusters\": " + std::to_string(cluster_max_active()) +
                  ", \"cluster_ctas\": " + std::to_string(cluster_ctas());
+    }
+    if (!p->dims.empty()) {
+        j += ", \"dims\": [";
+        for (size_t i = 0; i < p->dims.size(); i++) j += (i ? ", " : "") + std::to_string(p->dims[i]);
+        j += "], \"axes\": [";
+        for (size_t i = 0; i < p->axes.size(); i++) {
+            const AxisPlan &ax = p->axes[i];
+            j += (i ? ", [" : "[");
+            for (int k = 0; k < ax.npass; k++) {
+                const PassDesc &d = ax.pass[k];
+                j += (k ? ", " : "") + std::string("{\"log_r\": ") + std::to_string(d.log_r) + ", \"A\": " +
+                     std::to_string(d.A) + ", \"B\": " + std::to_string(d.B) + ", \"width\": " +
+                     std::to_string(d.width) + ", \"tw_mode\": " + std::to_string(d.tw_mode) + "}";
+            }
+            j += "]";
+        }
+        j += "]";
     }
     j += ", \"classes\": [";
     for (size_t i = 0; i < p->classes.size(); i++) {

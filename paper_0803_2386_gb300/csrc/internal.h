@@ -10,6 +10,7 @@
 namespace moafft {
 
 constexpr int kMaxPasses = 8;  // log2 n <= 40 with tiles of >= 2^5
+constexpr int kMaxDims = 8;    // axes of a multi-dimensional plan
 constexpr int kMaxSub = 13;    // register sub-passes per tile (13 x radix-2 at most)
 
 // One HBM pass of the dimension-lifted signal.  The transform of length n
@@ -35,7 +36,12 @@ struct PassDesc {
     size_t tw_pass_off = 0;
     size_t tw_hi_off = 0;
     size_t tw_digit_off = 0;
+    int col_shift = 0;           // PassArgs::col_shift
+    int64_t col_prev = 0;        // PassArgs::col_prev
 };
+
+// PassArgs::tw_mode of a column pass without pass weights
+constexpr int kTwNone = 4;
 
 struct Schedule {
     int64_t n = 1;
@@ -81,7 +87,9 @@ struct PassArgs {
     //      w_M^(e << lo_bits);
     //   2: rows by k: tw_pass[k B + b] (a warp's columns are consecutive);
     //   3: rows by the digits of k = r + U j, U = R / 16: tw_pass[r B + b] =
-    //      w_M^(b r), tw_hi[j B + b] = w_M^(b U j).
+    //      w_M^(b r), tw_hi[j B + b] = w_M^(b U j);
+    //   kTwNone: no pass weights -- a column pass that is a whole 1-D
+    //      transform along a strided axis (multi-dimensional plans).
     const void *tw_pass;
     const void *tw_hi;
     int tw_lo_bits;
@@ -94,6 +102,14 @@ struct PassArgs {
     int off_even;  // every offset is a multiple of 2 points (16-byte rows)
     int64_t off_align;    // largest power of two (<= 1024) dividing every offset
     int64_t total_elems;  // ragged batches: points in the packed buffer
+    // Column passes along a strided axis of a multi-dimensional plan: the
+    // weight tables' column is b >> col_shift (their rows hold B >> col_shift
+    // entries); col_prev = P > 0 marks the pass that finishes a two-pass
+    // axis transform, whose tiles store point k of line a at row
+    // (a / P) * P * R + a % P + P * k instead of a * R + k.  Both 0 in 1-D
+    // plans.
+    int col_shift;
+    int64_t col_prev;
     // device word set to 1 when a bounded wait inside a kernel gave up
     int *err;
     // tensor-core form: the split 32x32 DFT matrix of this direction, hi

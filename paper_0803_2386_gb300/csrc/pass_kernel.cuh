@@ -74,10 +74,11 @@ __device__ __forceinline__ typename cvec<T>::type pass_weight(const PassArgs &p,
     using V = typename cvec<T>::type;
     const V *t0 = reinterpret_cast<const V *>(p.tw_pass);
     const V *t1 = reinterpret_cast<const V *>(p.tw_hi);
-    if (p.tw_mode == 2) return __ldg(t0 + (int64_t)k * p.B + b);
+    const int64_t ld = p.B >> p.col_shift;  // entries per table row
+    if (p.tw_mode == 2) return __ldg(t0 + (int64_t)k * ld + b);
     if (p.tw_mode == 3) {
         const int ul = p.log_r - 4;
-        return c_mul(__ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * p.B + b), __ldg(t1 + (int64_t)(k >> ul) * p.B + b));
+        return c_mul(__ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * ld + b), __ldg(t1 + (int64_t)(k >> ul) * ld + b));
     }
     const int64_t e = b * (int64_t)k;
     if (p.tw_lo_bits == 0) return __ldg(t0 + e);
@@ -141,7 +142,12 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
         const int64_t b0 = (rem - a * colgroups) * W;
         const int64_t inner = a * (int64_t)R * p.B + b0;
         const int64_t base = (p.in_off ? p.in_off[tr] : tr * n) + inner;
-        const int64_t sbase = (p.out_off ? p.out_off[tr] : tr * n) + inner;
+        // the last pass of a strided axis stores through the axis's final
+        // transpose (PassArgs::col_prev)
+        const int64_t P = p.col_prev;
+        const int64_t sinner = P ? ((a / P) * P * R + a % P) * p.B + b0 : inner;
+        const int64_t kst = P ? P * p.B : p.B;
+        const int64_t sbase = (p.out_off ? p.out_off[tr] : tr * n) + sinner;
         for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
             int w = idx % W, m = idx / W;
             tile[spad(m * W + w)] = in[base + (int64_t)m * p.B + w];
@@ -161,8 +167,10 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
         for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
             int w = idx % W, k = idx / W;
             V v = tile[spad(tile_pos(k, p) * W + w)];
-            if (b0 + w != 0 && k != 0) v = c_tw<DIR>(v, pass_weight<T, DIR>(p, b0 + w, k));  // w_{R*B}^(b*k)
-            out[sbase + (int64_t)k * p.B + w] = v;
+            const int64_t bw = (b0 + w) >> p.col_shift;
+            if (p.tw_mode != kTwNone && bw != 0 && k != 0)
+                v = c_tw<DIR>(v, pass_weight<T, DIR>(p, bw, k));  // w_{R*B}^(b*k)
+            out[sbase + (int64_t)k * kst + w] = v;
         }
     } else {
         // ---- row tile: W rows with consecutive rev(a) (or W transforms when A = 1)

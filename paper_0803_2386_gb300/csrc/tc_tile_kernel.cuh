@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) tc_tile_kernel(PassArgs
         for (int j = 0; j < 16; j++) {
             const int kk = revu + U * j;
             V x = v[j];
-            if (b != 0 && kk != 0) {
+            if (p.tw_mode != kTwNone && b != 0 && kk != 0) {
                 const V wv = p.tw_mode == 3
                                  ? c_mul(wr, __ldg(reinterpret_cast<const V *>(p.tw_hi) + (int64_t)j * p.B + b))
                                  : pass_weight_at<float>(p, b, kk);

@@ -106,10 +106,11 @@ __device__ __forceinline__ typename cvec<T>::type pass_weight_at(const PassArgs 
     using M = MemOf<T>;
     const V *t0 = reinterpret_cast<const V *>(p.tw_pass);
     const V *t1 = reinterpret_cast<const V *>(p.tw_hi);
-    if (p.tw_mode == 2) return M::ldg(t0 + (int64_t)k * p.B + b);
+    const int64_t ld = p.B >> p.col_shift;  // entries per table row
+    if (p.tw_mode == 2) return M::ldg(t0 + (int64_t)k * ld + b);
     if (p.tw_mode == 3) {
         const int ul = p.log_r - 4;
-        return c_mul(M::ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * p.B + b), M::ldg(t1 + (int64_t)(k >> ul) * p.B + b));
+        return c_mul(M::ldg(t0 + (int64_t)(k & ((1 << ul) - 1)) * ld + b), M::ldg(t1 + (int64_t)(k >> ul) * ld + b));
     }
     const int64_t ex = b * (int64_t)k;
     if (p.tw_lo_bits == 0) return M::ldg(t0 + ex);
@@ -135,6 +136,7 @@ inline bool tile_covers(const PassArgs &a)
 // barrier, so the tile can run inside a persistent kernel.
 struct TileRef {
     int64_t base = 0, sbase = 0, b0 = 0, tr = 0, vrow = 0;
+    int64_t kstride = 0;  // column tiles: store stride of the tile index k
     bool valid = true;
 };
 
@@ -169,9 +171,14 @@ __device__ __forceinline__ TileRef tile_ref(const PassArgs &p, const int64_t cta
         const int64_t a = rem / colgroups;
         b0 = (rem - a * colgroups) * W;
         const int64_t inner = a * (int64_t)R * p.B + b0 + w;  // element (m, this column) at base + m*B
+        // output k at sbase + k * kstride: in place, or (the last pass of a
+        // strided axis) the axis's final transpose
+        const int64_t sinner =
+            p.col_prev ? ((a / p.col_prev) * p.col_prev * R + a % p.col_prev) * p.B + b0 + w : inner;
+        r.kstride = p.col_prev ? p.col_prev * p.B : p.B;
         if (valid) {
             base = (p.in_off ? __ldg(p.in_off + tr) : tr * n) + inner;
-            sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n) + inner;
+            sbase = (p.out_off ? __ldg(p.out_off + tr) : tr * n) + sinner;
         }
     } else {
         int64_t a;
@@ -359,26 +366,28 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     }
     if (!valid) return;
     if constexpr (!LAST) {
-        const int64_t b = b0 + w;
+        const int64_t b = (b0 + w) >> p.col_shift;  // the weights' column
+        const int64_t ks = r.kstride;
         if (p.tw_mode == 3) {
             // k = revu + U j: the digit-r factor w_M^(b revu) is this
             // thread's, the rest is one row of the second table per j
+            const int64_t ld = p.B >> p.col_shift;
             const V *t1 = reinterpret_cast<const V *>(p.tw_hi) + b;
-            const V wr = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + (int64_t)revu * p.B + b);
+            const V wr = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + (int64_t)revu * ld + b);
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 const int kk = revu + U * j;
                 V x = v[j];
-                if (b != 0 && kk != 0) x = c_tw<DIR>(x, c_mul(wr, M::ldg(t1 + (int64_t)j * p.B)));
-                M::store(out + sbase + (int64_t)kk * p.B, x);
+                if (b != 0 && kk != 0) x = c_tw<DIR>(x, c_mul(wr, M::ldg(t1 + (int64_t)j * ld)));
+                M::store(out + sbase + (int64_t)kk * ks, x);
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 const int kk = revu + U * j;  // NS == 1: R = 16, U = 1, revu = 0
                 V x = v[j];
-                if (b != 0 && kk != 0) x = c_tw<DIR>(x, pass_weight_at<T>(p, b, kk));
-                M::store(out + sbase + (int64_t)kk * p.B, x);
+                if (p.tw_mode != kTwNone && b != 0 && kk != 0) x = c_tw<DIR>(x, pass_weight_at<T>(p, b, kk));
+                M::store(out + sbase + (int64_t)kk * ks, x);
             }
         }
     } else {

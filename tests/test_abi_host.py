@@ -183,3 +183,21 @@ def test_register_digit_schedules():
     assert [sum(p["sub_log"]) for p in s["passes"]] == [7, 6] and s["passes"][0]["sub_log"] == [1] * 7
     assert "8/1,8/1" in M.fft_tune_candidates(1 << 16, M.FFT_C64)
 
+
+
+def test_plan_nd_argument_errors():
+    """fft_plan_nd validates its shape before touching the GPU."""
+    cases = [
+        (([64, 5000], 1), "NOT_POW2"),
+        (([1 << 25, 2], 1), "UNSUPPORTED"),         # an axis before the last above 2^24
+        (([4096, 4096, 8192], 1), "UNSUPPORTED"),   # 2^37 points per array
+        (([], 1), "FFT_ERR_ARG"),
+        (([2] * 9, 1), "FFT_ERR_ARG"),
+        (([16, 16], 0), "FFT_ERR_ARG"),
+        (([16, 0], 1), "FFT_ERR_ARG"),
+    ]
+    for (dims, batch), code in cases:
+        with pytest.raises(M.MoaFFTError, match=code):
+            M.fft_plan_nd(dims, batch, M.FFT_C64, M.FFT_FORWARD)
+    with pytest.raises(M.MoaFFTError, match="FFT_ERR_DTYPE"):
+        M.fft_plan_nd([16, 16], 1, 7, M.FFT_FORWARD)
