@@ -126,14 +126,15 @@ int fft_plan_many(fft_plan_t *out, const int64_t *sizes, int64_t count, fft_dtyp
  * most 2^36 points per array.  X[k_0..k_{d-1}] = sum over n of x[n] * prod_i
  * exp(s 2 pi i n_i k_i / dims[i]); the inverse is scaled by 1 / prod(dims).
  * The paper notes that multi-dimensional FFTs are built from the 1-D one
- * (Sec. "Conclusions for the General Radix Approach", footnote); here
- * the last axis runs as a batch of 1-D transforms (any length) and every
- * other axis as one column pass over its strided lines, in place on the
- * output, so each axis before the last takes at most 2^12 points
- * (FFT_ERR_UNSUPPORTED beyond).  Axes of length 1 are skipped.  Plain form
- * only.  Run it with fft_exec / fft_exec_adjoint (fft_exec_host returns
- * FFT_ERR_UNSUPPORTED for these plans).  Errors as fft_plan, plus
- * FFT_ERR_ARG for dims == NULL or ndim outside 1..8. */
+ * (Sec. "Conclusions for the General Radix Approach", footnote); here the
+ * last axis runs as a batch of 1-D transforms (any length) and every other
+ * axis as column passes over its strided lines: one pass in place on the
+ * output, or, for long axes (complex64 from 2^9 points, complex128 from
+ * 2^13), two passes through the plan's workspace.  Axes before the last
+ * take at most 2^24 points (FFT_ERR_UNSUPPORTED beyond); axes of length 1
+ * are skipped.  Plain form only.  Run it with fft_exec / fft_exec_adjoint
+ * (fft_exec_host returns FFT_ERR_UNSUPPORTED for these plans).  Errors as
+ * fft_plan, plus FFT_ERR_ARG for dims == NULL or ndim outside 1..8. */
 int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64_t batch, fft_dtype dt,
                 fft_dir dir);
 

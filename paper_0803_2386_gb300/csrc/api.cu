@@ -928,7 +928,10 @@ extern "C" int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64
         const int lg = exact_log2(d[i]);
         const int64_t S = per / (A * d[i]);
         const int64_t wt = (lg >= 4 && lg <= 12) ? std::min(32, std::max(1, 4096 >> lg)) : 16;
-        if (lg < 8 || (lg <= 12 && wt * (int64_t)eb >= 128)) {
+        // complex128 passes are FP64-bound: a second pass and its weights
+        // cost more than narrow tiles (2-D 2048^2 x 16: 8.7 ms one pass,
+        // 8.9-9.4 ms two), so only axes beyond one tile take two
+        if (lg < 8 || (lg <= 12 && (dt == FFT_C128 || wt * (int64_t)eb >= 128))) {
             PassDesc &q = ax.pass[0];
             q.log_r = lg;
             q.A = A;
@@ -950,11 +953,11 @@ extern "C" int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64
             ax.pass[0].A = A;
             ax.pass[0].B = s1.pass[0].B * S;
             ax.pass[0].col_shift = exact_log2(S);
-            // every lane of a warp reads the same weight column b (W <= S):
-            // the digit split keeps the two small tables in L1, where the
-            // whole-table rows of mode 2 (measured: 32 KB at L = 2^12) missed
-            // and left the pass latency-bound
-            ax.pass[0].tw_mode = 3;
+            // complex64: every lane of a warp reads the same weight column b
+            // (W <= S); the digit split keeps the two small tables in L1,
+            // where the whole-table rows of mode 2 (32 KB at L = 2^12) missed
+            // and left the pass latency-bound (1.02 -> 0.45 ms, 2-D 4096^2 x 8)
+            if (dt == FFT_C64) ax.pass[0].tw_mode = 3;
             ax.pass[0].width = width_for(s1.pass[0].log_r, ax.pass[0].B);
             ax.pass[1] = s1.pass[1];
             ax.pass[1].A = A * R0;
