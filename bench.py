@@ -580,6 +580,25 @@ def extra_configs(M, torch, dev, stream):
     ms_g = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
     launches = M.fft_plan_launches(pm)
     M.fft_destroy(pm)
+    # the same plan after the autotuner has timed every candidate schedule of
+    # each length at its count (a fresh cache file, so nothing is reused)
+    import tempfile
+    old_cache = os.environ.get("MOAFFT_TUNE_CACHE")
+    with tempfile.TemporaryDirectory() as tdir:
+        os.environ["MOAFFT_TUNE_CACHE"] = os.path.join(tdir, "tune.jsonl")
+        t_tune = time.perf_counter()
+        lengths, counts = np.unique(sizes, return_counts=True)
+        for s_, c_ in zip(lengths.tolist(), counts.tolist()):
+            M.Plan(int(s_), int(c_), M.FFT_C64, M.FFT_FORWARD, M.FFT_FORM_PLAIN, "auto").close()
+        tune_s = time.perf_counter() - t_tune
+        pm = M.fft_plan_many(sizes, M.FFT_C64, M.FFT_FORWARD)
+        ms_t = _time(torch, stream, lambda: M.fft_exec(pm, xu, yu, stream), 10)
+        M.fft_plan_check(pm)
+        M.fft_destroy(pm)
+    if old_cache is None:
+        del os.environ["MOAFFT_TUNE_CACHE"]
+    else:
+        os.environ["MOAFFT_TUNE_CACHE"] = old_cache
     plans = {}
     offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
 
@@ -597,6 +616,7 @@ def extra_configs(M, torch, dev, stream):
            "persistent_ms": round(ms_pers, 3), "persistent": pers,
            "persistent_gflops": round(fl / (ms_pers * 1e-3) / 1e9, 1), "graph_ms": round(ms_g, 3),
            "graph_launches": launches, "graph_gflops": round(fl / (ms_g * 1e-3) / 1e9, 1),
+           "graph_autotuned_ms": round(ms_t, 3), "autotune_s": round(tune_s, 1),
            "per_transform_launch_ms": round(ms_p, 3), "speedup": round(ms_p / ms_g, 1)})
     del xu, yu
 
