@@ -172,6 +172,7 @@ def cpu_baseline(n: int, batch: int, target_s: float = 12.0, rows=None):
     import workloads as W
     cores = os.cpu_count() or 1
     x1 = W.uniform_complex(n, 1, seed=0)
+    O.lib()  # load (and if needed build) before timing
     t0 = time.perf_counter()
     O.fft(x1, "forward", c=1024, threads=1)
     t1 = max(time.perf_counter() - t0, 1e-3)
@@ -190,6 +191,9 @@ def cpu_baseline(n: int, batch: int, target_s: float = 12.0, rows=None):
     out = {"value": round(gflops, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"{s} of the {batch} transforms of n=2^{int(math.log2(n))}, forward+inverse, "
                      f"{threads} threads, {dt:.2f} s wall"}
+    # the single-threaded setting: the one forward transform that sized the sample
+    out["single_thread"] = {"value": round(5.0 * n * math.log2(n) / t1 / 1e9, 4), "unit": UNIT, "cores": 1,
+                            "sample": f"one forward transform of n=2^{int(math.log2(n))}, {t1:.3f} s"}
     if Xg is not None:
         err = np.linalg.norm(Xg - X, axis=-1) / np.linalg.norm(X, axis=-1)
         out["gpu_vs_oracle_rel_err"] = {"transforms": int(s), "max": float(err.max()),
