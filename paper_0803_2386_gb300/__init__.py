@@ -453,3 +453,46 @@ def fft_autograd(x, inverse: bool = False, form: int = FFT_FORM_PLAIN, schedule=
     if _FFTFunction is None:
         _FFTFunction = _make_autograd()
     return _FFTFunction.apply(x, inverse, form, schedule)
+
+
+def _make_autograd_nd():
+    import torch
+
+    class FFTNFunction(torch.autograd.Function):
+        """y = F x over the last `ndim` axes (fft_plan_nd); backward applies
+        the adjoint F^H through fft_exec_adjoint."""
+
+        @staticmethod
+        def forward(ctx, x, ndim, inverse=False):
+            x = x.contiguous()
+            dims = tuple(x.shape[x.dim() - ndim:])
+            batch = x.numel() // max(math.prod(dims), 1)
+            key = ("nd", dims, batch, _dtype_code(x), inverse, torch.cuda.current_device())
+            p = _PLAN_CACHE.get(key)
+            if p is None:
+                p = PlanND(dims, batch, _dtype_code(x), FFT_INVERSE if inverse else FFT_FORWARD)
+                _PLAN_CACHE[key] = p
+            ctx.plan = p
+            out = torch.empty_like(x)
+            p.exec(x, out)
+            return out
+
+        @staticmethod
+        def backward(ctx, g):
+            g = g.contiguous()
+            gx = torch.empty_like(g)
+            ctx.plan.exec_adjoint(g, gx)
+            return gx, None, None
+
+    return FFTNFunction
+
+
+_FFTNFunction = None
+
+
+def fftn_autograd(x, ndim: int | None = None, inverse: bool = False):
+    """Differentiable transform of the last `ndim` axes (default: all)."""
+    global _FFTNFunction
+    if _FFTNFunction is None:
+        _FFTNFunction = _make_autograd_nd()
+    return _FFTNFunction.apply(x, x.dim() if ndim is None else ndim, inverse)
