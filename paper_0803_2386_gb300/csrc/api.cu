@@ -493,6 +493,10 @@ struct fft_plan_s {
     std::vector<cudaEvent_t> ev_free;
     // host-buffer pipeline (fft_exec_host), created on first use
     DevBuf stage_in[2], stage_out[2];
+    // per slot: the workspace of multi-pass plans and the stream the slot's
+    // transform runs on, so consecutive slices overlap on the GPU
+    DevBuf stage_ws[2];
+    cudaStream_t s_comp[2] = {nullptr, nullptr};
     int64_t stage_tr = 0;  // transforms per staging slot
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
@@ -700,6 +704,8 @@ static void destroy_plan(fft_plan_s *p)
     for (int k = 0; k < 2; k++) {
         dev_free(p->stage_in[k]);
         dev_free(p->stage_out[k]);
+        dev_free(p->stage_ws[k]);
+        if (p->s_comp[k]) cudaStreamDestroy(p->s_comp[k]);
         if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
         if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
         if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
@@ -1224,9 +1230,10 @@ static int check_device_ptr(const void *ptr, size_t align, const char *what)
 // in/out are the whole packed buffers and the offset table locates each
 // transform.
 static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *out, int64_t t0,
-                      int64_t cnt, int sign, cudaStream_t s)
+                      int64_t cnt, int sign, cudaStream_t s, void *ws = nullptr)
 {
     size_t eb = elem_bytes(p->dt);
+    void *const wsp = ws ? ws : p->ws.ptr;  // workspace of the passes between the first and the last
     const Schedule &S = C.sched;
     const double scale = class_scale(p, C);
     const bool ragged = C.d_off.ptr != nullptr;
@@ -1234,7 +1241,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
         if (ragged) return fail(FFT_ERR_UNSUPPORTED, "the per-stage schedule takes dense batches");
         const char *src = (const char *)in + (size_t)t0 * C.n * eb;
         char *dst = (char *)out + (size_t)t0 * C.n * eb;
-        cudaError_t e = launch_stages(p->dt == FFT_C128, S.stride_order, src, dst, p->ws.ptr, C.n, cnt,
+        cudaError_t e = launch_stages(p->dt == FFT_C128, S.stride_order, src, dst, wsp, C.n, cnt,
                                       (const char *)p->tw.ptr + S.pass[0].tw_pass_off * eb, sign, scale, s);
         if (e != cudaSuccess) return fail_cuda(e, "per-stage launch");
         return FFT_OK;
@@ -1275,8 +1282,8 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
         const int64_t *off = ragged ? (const int64_t *)C.d_off.ptr + t0 + c0 : nullptr;
         for (int i = 0; i < S.npass; i++) {
             const PassDesc &d = S.pass[i];
-            a.in = (i == 0) ? (const void *)src : p->ws.ptr;
-            a.out = (i == S.npass - 1) ? (void *)dst : p->ws.ptr;
+            a.in = (i == 0) ? (const void *)src : wsp;
+            a.out = (i == S.npass - 1) ? (void *)dst : wsp;
             a.in_off = (i == 0) ? off : nullptr;
             a.out_off = (i == S.npass - 1) ? off : nullptr;
             a.off_even = C.off_even ? 1 : 0;
@@ -1535,16 +1542,24 @@ static int setup_staging(fft_plan_t p)
 {
     if (p->stage_tr > 0) return FFT_OK;
     size_t eb = elem_bytes(p->dt);
+    // 64 MiB slots (measured on the bench's complex128 step, 2^20 x 64:
+    // slots of 16 / 32 / 64 / 128 MiB gave 611 / 700 / 701 / 680 GFLOP/s
+    // end to end)
     const int64_t slot_bytes = (int64_t)64 << 20;
     int64_t tr = std::max<int64_t>(1, slot_bytes / (p->n * (int64_t)eb));
     tr = std::min(tr, p->batch);
     size_t bytes = (size_t)tr * p->n * eb;
+    const SizeClass &C = p->classes[0];
+    const bool needs_ws = C.sched.unblocked || C.sched.npass > 1;
     for (int k = 0; k < 2; k++) {
         int st = dev_alloc(p->stage_in[k], bytes, "host staging (in)");
         if (st == FFT_OK) st = dev_alloc(p->stage_out[k], bytes, "host staging (out)");
+        if (st == FFT_OK && needs_ws) st = dev_alloc(p->stage_ws[k], bytes, "host staging (workspace)");
         if (st != FFT_OK) return st;
     }
-    cudaError_t e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamCreateWithFlags(&p->s_comp[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; k++) {
@@ -1557,8 +1572,10 @@ static int setup_staging(fft_plan_t p)
     return FFT_OK;
 }
 
-// Slice i uses slot i % 2: H2D on s_h2d, transform on the caller's stream,
-// D2H on s_d2h; events order the reuse of each slot.
+// Slice i uses slot i % 2: H2D on s_h2d, transform on the slot's stream
+// s_comp[k] (so one slice's last wave overlaps the next slice's first), D2H
+// on s_d2h; events order the reuse of each slot, and the caller's stream
+// waits for the last copies out.
 static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
 {
     if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
@@ -1580,6 +1597,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
     {
         cudaError_t e = cudaEventRecord(p->ev_start, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_h2d, p->ev_start, 0);
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(p->s_comp[k], p->ev_start, 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (stream order)");
     }
     for (int64_t b0 = 0, i = 0; b0 < p->batch; b0 += p->stage_tr, i++) {
@@ -1591,13 +1609,14 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->stage_in[k].ptr, (const char *)in + off, bytes, cudaMemcpyHostToDevice,
                                 p->s_h2d);
+        cudaStream_t ks = p->s_comp[k];
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_h2d[k], p->s_h2d);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, p->ev_h2d[k], 0);
-        if (e == cudaSuccess && used[k]) e = cudaStreamWaitEvent(cs, p->ev_d2h[k], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, p->ev_h2d[k], 0);
+        if (e == cudaSuccess && used[k]) e = cudaStreamWaitEvent(ks, p->ev_d2h[k], 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (copy in)");
-        st = exec_class(p, C, p->stage_in[k].ptr, p->stage_out[k].ptr, 0, cnt, sign, cs);
+        st = exec_class(p, C, p->stage_in[k].ptr, p->stage_out[k].ptr, 0, cnt, sign, ks, p->stage_ws[k].ptr);
         if (st != FFT_OK) return st;
-        e = cudaEventRecord(p->ev_comp[k], cs);
+        e = cudaEventRecord(p->ev_comp[k], ks);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, p->ev_comp[k], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync((char *)out + off, p->stage_out[k].ptr, bytes, cudaMemcpyDeviceToHost,
