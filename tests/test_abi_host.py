@@ -107,6 +107,25 @@ def test_default_schedule_covers_all_stages(t, dt):
     assert s["passes"][-1]["B"] == 1
 
 
+def test_default_schedule_splits():
+    """One pass up to 2^12 points; complex64 beyond takes the split measured
+    fastest on GB300 (column tiles of at least 4 columns, a third pass from
+    2^21); complex128 balanced passes of at most 2^11."""
+    c64 = {13: [7, 6], 14: [7, 7], 15: [7, 8], 16: [8, 8], 17: [8, 9], 18: [8, 10], 19: [9, 10],
+           20: [10, 10], 21: [7, 7, 7], 22: [7, 7, 8], 23: [7, 8, 8], 24: [8, 8, 8]}
+    for t in range(0, 31):
+        for dt in (M.FFT_C64, M.FFT_C128):
+            radices = [p["log_r"] for p in json.loads(M.fft_describe_schedule(1 << t, dt))["passes"]]
+            if t <= 12:
+                assert radices == [t], (t, dt)
+            elif dt == M.FFT_C64 and t in c64:
+                assert radices == c64[t], t
+            else:
+                cap = 11 if dt == M.FFT_C128 else 10
+                g = -(-t // cap)
+                assert len(radices) == g and max(radices) - min(radices) <= 1 and max(radices) <= cap
+
+
 def test_explicit_schedule_parse():
     s = json.loads(M.fft_describe_schedule(1 << 12, M.FFT_C64, M.FFT_FORM_PLAIN, "4@8,4,4"))
     assert [p["log_r"] for p in s["passes"]] == [4, 4, 4]
