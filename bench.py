@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the host-buffer measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64", "dm"],
+    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64", "dm", "nd2d"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -778,6 +778,18 @@ def run_case(args):
     import torch
     import paper_0803_2386_gb300 as M
     torch.manual_seed(0)
+    if args.case == "nd2d":  # 2-D complex64 4096 x 4096 x 2 (256 MiB): last axis, then two axis passes
+        dims = (4096, 4096)
+        gen = torch.Generator(device="cuda").manual_seed(2)
+        x = torch.randn((2,) + dims, dtype=torch.complex64, device="cuda", generator=gen)
+        y = torch.empty_like(x)
+        with M.PlanND(dims, 2, M.FFT_C64, M.FFT_FORWARD) as p:
+            for _ in range(args.steps):
+                p.exec(x, y)
+            torch.cuda.synchronize()
+            M.fft_plan_check(p.handle)
+        print("ok")
+        return 0
     if args.case == "dm":  # density-matrix gate: 13 qubits, complex64 (512 MiB), qubit 0
         import numpy as np
         gen = torch.Generator(device="cuda").manual_seed(13)
