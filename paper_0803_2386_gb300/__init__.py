@@ -399,6 +399,8 @@ def fftn(x, ndim: int | None = None, inverse: bool = False):
     import torch
     x = x.contiguous()
     ndim = x.dim() if ndim is None else ndim
+    if not 1 <= ndim <= min(x.dim(), 8):
+        raise ValueError(f"fftn: ndim = {ndim} for a tensor of {x.dim()} axes (1..8 axes)")
     dims = tuple(x.shape[x.dim() - ndim:])
     batch = x.numel() // max(math.prod(dims), 1)
     key = ("nd", dims, batch, _dtype_code(x), inverse, torch.cuda.current_device())
@@ -495,4 +497,7 @@ def fftn_autograd(x, ndim: int | None = None, inverse: bool = False):
     global _FFTNFunction
     if _FFTNFunction is None:
         _FFTNFunction = _make_autograd_nd()
-    return _FFTNFunction.apply(x, x.dim() if ndim is None else ndim, inverse)
+    ndim = x.dim() if ndim is None else ndim
+    if not 1 <= ndim <= min(x.dim(), 8):
+        raise ValueError(f"fftn_autograd: ndim = {ndim} for a tensor of {x.dim()} axes (1..8 axes)")
+    return _FFTNFunction.apply(x, ndim, inverse)

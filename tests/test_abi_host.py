@@ -220,3 +220,13 @@ def test_plan_nd_argument_errors():
             M.fft_plan_nd(dims, batch, M.FFT_C64, M.FFT_FORWARD)
     with pytest.raises(M.MoaFFTError, match="FFT_ERR_DTYPE"):
         M.fft_plan_nd([16, 16], 1, 7, M.FFT_FORWARD)
+
+
+def test_fftn_wrapper_rejects_bad_axis_counts():
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(2, 4, 8, dtype=torch.complex64)
+    for nd in (0, 4, 9):
+        with pytest.raises(ValueError):
+            M.fftn(x, ndim=nd)
+        with pytest.raises(ValueError):
+            M.fftn_autograd(x, ndim=nd)
