@@ -138,11 +138,22 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- helpers
 
+def code_text(src: str) -> str:
+    """A kernel source without its comments and blank space: what the
+    traffic record's key tracks (a comment edit leaves the code, and so the
+    recorded DRAM traffic, unchanged)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def source_hash() -> str:
     h = hashlib.sha1()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_0803_2386_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:12]
 
 

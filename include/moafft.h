@@ -105,7 +105,7 @@ int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir di
  * Fig. fftpsirad2) and "cluster" (complex64, n = 2^16, plain form only: one
  * HBM round trip, the reshape-transpose carried by the distributed shared
  * memory of a thread-block cluster; FFT_ERR_UNSUPPORTED elsewhere).  The
- * paper lets the user choose the block size c at run time (Ch.2); a pass
+ * paper lets the user choose the block size c at run time (Ch.1, Ch.3); a pass
  * of log2 radix r is a group of r
  * radix-2 stages. */
 int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir dir,

@@ -333,7 +333,7 @@ static std::string schedule_json(const Schedule &s)
 // ------------------------------------------------------------ autotuner ---
 //
 // The paper leaves the block size c to the user at run time so that each
-// machine can use its best one (Ch.2; Table 4 sweeps the radix).  Here the choice is searched: candidate
+// machine can use its best one (Ch.1, Ch.3; Table 4 sweeps the radix).  Here the choice is searched: candidate
 // pass schedules (how log2 n splits into HBM passes, and how many transforms
 // a workspace round holds) are timed on the GPU and the fastest is cached.
 
