@@ -250,7 +250,7 @@ int fft_set_allocator(fft_alloc_fn alloc, fft_free_fn release, void *ctx);
  * named by $MOAFFT_TUNE_CACHE (default $HOME/.cache/moafft_tune.jsonl), keyed
  * by GPU name, n, batch (power-of-two bucket), dtype and form; plans created
  * with a NULL or "" schedule, and the size classes of fft_plan_many, use a
- * cached winner when there is one.  Cite: Ch.2 (block size chosen at run
+ * cached winner when there is one.  Cite: Ch.1, Ch.3 (block size chosen at run
  * time) and Table 4 (the radix sweep). */
 int fft_tune_candidates(int64_t n, fft_dtype dt, fft_form form, char *buf, int64_t len);
 
