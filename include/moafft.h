@@ -76,7 +76,7 @@ typedef enum {
     FFT_ERR_ALLOC = -5,       /* device allocation failed */
     FFT_ERR_CUDA = -6,        /* a CUDA runtime call or kernel failed */
     FFT_ERR_TIMEOUT = -7,     /* a bounded device-side wait gave up */
-    FFT_ERR_UNSUPPORTED = -8  /* valid request this build does not provide */
+    FFT_ERR_UNSUPPORTED = -8  /* valid request the library does not provide */
 } fft_status;
 
 /* Create a plan for `batch` transforms of length n.  Allocates the device
