@@ -13,6 +13,9 @@ binary64, no fused multiply-add).  What each one follows in the paper
   (Fig. vanloan_fft: "Output: the FFT of x"), brute force in long double.
 * :func:`fftpsirad2` -- Fig. fftpsirad2 / rad2_fft, preceded by the
   bit-reversal P_n of Fig. vanloan_fft line (1).
+* :func:`fftpsiradn` -- the general-radix routine (Fig. radnbutterfly):
+  base-digit reversal, then stages of direct base-point DFTs of weighted
+  inputs.
 * :func:`fftn` -- multi-dimensional transforms as 1-D transforms along
   every axis (Sec. "Conclusions for the General Radix Approach", footnote).
 * :func:`moa_fft` -- the cache-optimised algorithm of Ch.3 (Sec. butter-order
@@ -71,6 +74,8 @@ def lib():
             "dft_bins_c128": (ctypes.c_int, [_f64p, ctypes.c_int64, ctypes.c_int, _i64p,
                                              ctypes.c_int64, _f64p]),
             "fftpsirad2_c128": (ctypes.c_int, [_f64p, _f64p, ctypes.c_int64, ctypes.c_int]),
+            "fftpsiradn_c128": (ctypes.c_int, [_f64p, _f64p, ctypes.c_int64, ctypes.c_int64,
+                                               ctypes.c_int]),
             "moa_fft_c128": (ctypes.c_int, [_f64p, _f64p, ctypes.c_int64, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_int]),
             "oracle_fft_many": (ctypes.c_int, [_f64p, _f64p, ctypes.c_int64, ctypes.c_int64,
@@ -212,6 +217,14 @@ def fftpsirad2(x, sign: int = -1) -> np.ndarray:
     x = _c128(x)
     y = np.empty_like(x)
     _check(lib().fftpsirad2_c128(_fp(x), _fp(y), len(x), int(sign)), "fftpsirad2")
+    return y
+
+
+def fftpsiradn(x, base: int, sign: int = -1) -> np.ndarray:
+    """General-radix FFT (Fig. radnbutterfly): len(x) a power of `base`."""
+    x = _c128(x)
+    y = np.empty_like(x)
+    _check(lib().fftpsiradn_c128(_fp(x), _fp(y), len(x), int(base), int(sign)), "fftpsiradn")
     return y
 
 

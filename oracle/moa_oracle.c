@@ -11,6 +11,8 @@
  *   - fftpsirad2: the unblocked radix-2 routine (Fig. fftpsirad2 / rad2_fft)
  *     preceded by the bit-reversal P_n of Van Loan's program (Fig. vanloan_fft,
  *     line (1)), which the printed fragment assumes has been done.
+ *   - fftpsiradn: the general-radix routine (Sec. "Performance of the
+ *     General-Radix FFT", Fig. radnbutterfly) for n a power of the radix.
  *   - moa_fft: the cache-optimised algorithm of Ch.3: radix-2 stages inside
  *     rows of length c, reshape-transposes between groups of log2(c) stages
  *     (Eqs. reshape1-3, xdeqn), weights tracked through the transposes
@@ -392,6 +394,94 @@ int fftpsirad2_c128(const double *in, double *out, int64_t n, int sign)
     memcpy(out, x, sizeof(cplx) * (size_t)n);
     free(x);
     free(w);
+    return OR_OK;
+}
+
+/* The general-radix routine fftpsiradn (Sec. "Performance of the
+ * General-Radix FFT", Figs. rad2butterfly and radnbutterfly): n = base^l,
+ * base a power of two.  The input is first put in base-digit-reversed order
+ * (the radix-base analogue of P_n); stage s = 1..l then combines, for every
+ * group of base*L points (L = base^(s-1)) and every j < L, the `base` points
+ * spaced L apart: c_0 = z[i+j], c_k = w_(base L)^(j k) z[i+j+k L] for
+ * 0 < k < base, and z[i+j+k L] = sum_q c_q w_base^(k q), q = 0..base-1 in
+ * order (a direct base-point DFT of the weighted inputs).  The stage weights
+ * come from w_N^e computed as in weight_table; w_base^m is exact at the
+ * quarter turns, so base 2 performs the butterflies of fftpsirad2 bit for
+ * bit. */
+int fftpsiradn_c128(const double *in, double *out, int64_t n, int64_t base, int sign)
+{
+    int lb = exact_log2(base);
+    int t = exact_log2(n);
+    if (lb < 1 || t < 0 || t % lb != 0)
+        return lb < 1 ? OR_ERR_ARG : OR_ERR_NOT_POW2;
+    if (!in || !out || (sign != 1 && sign != -1))
+        return OR_ERR_ARG;
+    const int l = t / lb;
+    cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)n);      /* w_N^e, e < N */
+    cplx *wb = (cplx *)malloc(sizeof(cplx) * (size_t)base);  /* w_base^m */
+    cplx *x = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *c = (cplx *)malloc(sizeof(cplx) * (size_t)base);
+    if (!w || !wb || !x || !c) {
+        free(w);
+        free(wb);
+        free(x);
+        free(c);
+        return OR_ERR_ALLOC;
+    }
+    for (int64_t e = 0; e < n; e++) {
+        double ang = M_PI * ((2.0 * (double)e) / (double)n);
+        w[e].re = cos(ang);
+        w[e].im = (double)sign * sin(ang);
+    }
+    for (int64_t m = 0; m < base; m++) {
+        if ((4 * m) % base == 0) { /* quarter turns: exact */
+            const int64_t qt = (4 * m) / base;
+            wb[m].re = qt == 0 ? 1.0 : (qt == 2 ? -1.0 : 0.0);
+            wb[m].im = qt == 1 ? (double)sign : (qt == 3 ? -(double)sign : 0.0);
+        } else {
+            double ang = M_PI * ((2.0 * (double)m) / (double)base);
+            wb[m].re = cos(ang);
+            wb[m].im = (double)sign * sin(ang);
+        }
+    }
+    const cplx *src = (const cplx *)in;
+    for (int64_t k = 0; k < n; k++) { /* base-digit reversal */
+        int64_t r = 0, v = k;
+        for (int d = 0; d < l; d++) {
+            r = r * base + v % base;
+            v /= base;
+        }
+        x[r] = src[k];
+    }
+    int64_t L = 1;
+    for (int st = 1; st <= l; st++, L *= base) {
+        const int64_t M = base * L;
+        const int64_t step = n / M; /* w_M^e = w_N^(e n / M) */
+        for (int64_t i = 0; i < n; i += M)
+            for (int64_t j = 0; j < L; j++) {
+                c[0] = x[i + j];
+                for (int64_t k = 1; k < base; k++) {
+                    const cplx a = x[i + j + k * L];
+                    const cplx ww = w[j * k * step];
+                    c[k].re = ww.re * a.re - ww.im * a.im;
+                    c[k].im = ww.re * a.im + ww.im * a.re;
+                }
+                for (int64_t k = 0; k < base; k++) {
+                    cplx acc = c[0];
+                    for (int64_t q = 1; q < base; q++) {
+                        const cplx e = wb[(k * q) % base];
+                        acc.re += e.re * c[q].re - e.im * c[q].im;
+                        acc.im += e.re * c[q].im + e.im * c[q].re;
+                    }
+                    x[i + j + k * L] = acc;
+                }
+            }
+    }
+    memcpy(out, x, sizeof(cplx) * (size_t)n);
+    free(w);
+    free(wb);
+    free(x);
+    free(c);
     return OR_OK;
 }
 

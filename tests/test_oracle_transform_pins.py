@@ -166,3 +166,35 @@ def test_errors():
         O.moa_fft(np.zeros(12, complex), 4)
     with pytest.raises(O.OracleError):
         O.dft_direct(np.zeros(0, complex))
+
+
+# ---- general radix (Fig. radnbutterfly) ------------------------------------
+
+@pytest.mark.parametrize("base,n", [(2, 1), (2, 2), (4, 4), (4, 256), (8, 512), (16, 4096), (64, 4096),
+                                    (4, 1024), (2, 2048), (256, 256)])
+def test_fftpsiradn_matches_direct_dft(base, n):
+    """The general-radix routine against the definition (long double
+    accumulation), both exponent signs."""
+    rng = np.random.default_rng(base + n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for sign in (-1, 1):
+        got = O.fftpsiradn(x, base, sign)
+        ref = O.dft_direct(x, sign)
+        assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.log2(n)) * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("t", range(0, 13))
+def test_fftpsiradn_base2_is_fftpsirad2_bitwise(t):
+    """Radix 2 of the general routine performs the butterflies of
+    fftpsirad2 exactly (same weights, w_2 = -1 exact)."""
+    x = W.uniform_complex(1 << t, 1, seed=t)[0]
+    for sign in (-1, 1):
+        assert np.array_equal(O.fftpsiradn(x, 2, sign), O.fftpsirad2(x, sign))
+
+
+def test_fftpsiradn_rejects_lengths_that_are_not_powers_of_the_base():
+    x = np.ones(32, complex)
+    with pytest.raises(RuntimeError):
+        O.fftpsiradn(x, 4)   # 32 = 2^5 is not a power of 4
+    with pytest.raises(RuntimeError):
+        O.fftpsiradn(x, 3)   # radix 3 is outside the routine's domain (powers of two)
