@@ -398,90 +398,116 @@ int fftpsirad2_c128(const double *in, double *out, int64_t n, int sign)
 }
 
 /* The general-radix routine fftpsiradn (Sec. "Performance of the
- * General-Radix FFT", Figs. rad2butterfly and radnbutterfly): n = base^l,
- * base a power of two.  The input is first put in base-digit-reversed order
- * (the radix-base analogue of P_n); stage s = 1..l then combines, for every
- * group of base*L points (L = base^(s-1)) and every j < L, the `base` points
- * spaced L apart: c_0 = z[i+j], c_k = w_(base L)^(j k) z[i+j+k L] for
- * 0 < k < base, and z[i+j+k L] = sum_q c_q w_base^(k q), q = 0..base-1 in
- * order (a direct base-point DFT of the weighted inputs).  The stage weights
- * come from w_N^e computed as in weight_table; w_base^m is exact at the
- * quarter turns, so base 2 performs the butterflies of fftpsirad2 bit for
- * bit. */
+ * General-Radix FFT", Figs. rad2butterfly and radnbutterfly), n = base^l
+ * with base a power of two.
+ *
+ * Written here as a product of sparse operators (the Cooley-Tukey
+ * factorisation the figures implement):
+ *     X = A_l ... A_2 A_1 Q x,
+ * where Q reverses the base-digits of the index (the radix-base analogue of
+ * P_n), and stage s, with L = base^(s-1) and M = base*L, views z as the
+ * array Z[g][q][j] (g < n/M, q < base, j < L; position g*M + q*L + j) and
+ * applies
+ *     A_s = (I_(n/M) (x) F_base (x) I_L) * Omega_s,
+ * Omega_s the diagonal that multiplies Z[g][q][j] by w_M^(q*j), and F_base
+ * the base-point DFT matrix F[k][q] = w_base^(k*q), applied along q.  The
+ * weights w_M^e come from the table w_N^e (e < n), computed as in
+ * weight_table; F_base is exact at the quarter turns, so with base 2 the
+ * diagonal is fftpsirad2's weight product and F_2 its add/subtract: the two
+ * routines agree bit for bit. */
+
+/* base-digit reversal of k < base^l */
+static int64_t digit_reverse(int64_t k, int64_t base, int l)
+{
+    int64_t r = 0;
+    for (int d = 0; d < l; d++, k /= base)
+        r = r * base + k % base;
+    return r;
+}
+
+/* z <- z * w (the weight product, re/im in fftpsirad2's order) */
+static void scale_by(cplx *z, cplx w)
+{
+    const cplx a = *z;
+    z->re = w.re * a.re - w.im * a.im;
+    z->im = w.re * a.im + w.im * a.re;
+}
+
 int fftpsiradn_c128(const double *in, double *out, int64_t n, int64_t base, int sign)
 {
-    int lb = exact_log2(base);
-    int t = exact_log2(n);
+    const int lb = exact_log2(base);
+    const int t = exact_log2(n);
     if (lb < 1 || t < 0 || t % lb != 0)
         return lb < 1 ? OR_ERR_ARG : OR_ERR_NOT_POW2;
     if (!in || !out || (sign != 1 && sign != -1))
         return OR_ERR_ARG;
     const int l = t / lb;
-    cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)n);      /* w_N^e, e < N */
-    cplx *wb = (cplx *)malloc(sizeof(cplx) * (size_t)base);  /* w_base^m */
-    cplx *x = (cplx *)malloc(sizeof(cplx) * (size_t)n);
-    cplx *c = (cplx *)malloc(sizeof(cplx) * (size_t)base);
-    if (!w || !wb || !x || !c) {
-        free(w);
-        free(wb);
-        free(x);
-        free(c);
+    cplx *wn = (cplx *)malloc(sizeof(cplx) * (size_t)n);                /* w_N^e */
+    cplx *F = (cplx *)malloc(sizeof(cplx) * (size_t)(base * base));     /* F_base */
+    cplx *z = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *col = (cplx *)malloc(sizeof(cplx) * (size_t)base);
+    if (!wn || !F || !z || !col) {
+        free(wn);
+        free(F);
+        free(z);
+        free(col);
         return OR_ERR_ALLOC;
     }
     for (int64_t e = 0; e < n; e++) {
-        double ang = M_PI * ((2.0 * (double)e) / (double)n);
-        w[e].re = cos(ang);
-        w[e].im = (double)sign * sin(ang);
+        const double ang = M_PI * ((2.0 * (double)e) / (double)n);
+        wn[e].re = cos(ang);
+        wn[e].im = (double)sign * sin(ang);
     }
-    for (int64_t m = 0; m < base; m++) {
-        if ((4 * m) % base == 0) { /* quarter turns: exact */
-            const int64_t qt = (4 * m) / base;
-            wb[m].re = qt == 0 ? 1.0 : (qt == 2 ? -1.0 : 0.0);
-            wb[m].im = qt == 1 ? (double)sign : (qt == 3 ? -(double)sign : 0.0);
-        } else {
-            double ang = M_PI * ((2.0 * (double)m) / (double)base);
-            wb[m].re = cos(ang);
-            wb[m].im = (double)sign * sin(ang);
+    /* F[k][q] = w_base^(k q mod base); entries at quarter turns are exact */
+    for (int64_t k = 0; k < base; k++)
+        for (int64_t q = 0; q < base; q++) {
+            const int64_t m = (k * q) % base;
+            cplx f;
+            if ((4 * m) % base == 0) {
+                const int64_t quarter = (4 * m) / base;
+                f.re = quarter == 0 ? 1.0 : (quarter == 2 ? -1.0 : 0.0);
+                f.im = quarter == 1 ? (double)sign : (quarter == 3 ? -(double)sign : 0.0);
+            } else {
+                const double ang = M_PI * ((2.0 * (double)m) / (double)base);
+                f.re = cos(ang);
+                f.im = (double)sign * sin(ang);
+            }
+            F[k * base + q] = f;
         }
-    }
-    const cplx *src = (const cplx *)in;
-    for (int64_t k = 0; k < n; k++) { /* base-digit reversal */
-        int64_t r = 0, v = k;
-        for (int d = 0; d < l; d++) {
-            r = r * base + v % base;
-            v /= base;
-        }
-        x[r] = src[k];
-    }
-    int64_t L = 1;
-    for (int st = 1; st <= l; st++, L *= base) {
+    /* Q: z[digit_reverse(k)] = x[k] */
+    const cplx *x = (const cplx *)in;
+    for (int64_t k = 0; k < n; k++)
+        z[digit_reverse(k, base, l)] = x[k];
+    for (int64_t L = 1; L < n; L *= base) {
         const int64_t M = base * L;
-        const int64_t step = n / M; /* w_M^e = w_N^(e n / M) */
-        for (int64_t i = 0; i < n; i += M)
+        /* Omega_s: Z[g][q][j] *= w_M^(q j) = w_N^(q j n/M) */
+        for (int64_t g = 0; g < n / M; g++)
+            for (int64_t q = 1; q < base; q++)
+                for (int64_t j = 1; j < L; j++)
+                    scale_by(&z[g * M + q * L + j], wn[q * j * (n / M)]);
+        /* F_base along q, for every (g, j): Z[g][.][j] <- F Z[g][.][j] */
+        for (int64_t g = 0; g < n / M; g++)
             for (int64_t j = 0; j < L; j++) {
-                c[0] = x[i + j];
-                for (int64_t k = 1; k < base; k++) {
-                    const cplx a = x[i + j + k * L];
-                    const cplx ww = w[j * k * step];
-                    c[k].re = ww.re * a.re - ww.im * a.im;
-                    c[k].im = ww.re * a.im + ww.im * a.re;
-                }
+                cplx *v = z + g * M + j; /* element q at v[q L] */
+                for (int64_t q = 0; q < base; q++)
+                    col[q] = v[q * L];
                 for (int64_t k = 0; k < base; k++) {
-                    cplx acc = c[0];
+                    /* F[k][0] = 1: the sum starts from col[0] */
+                    cplx s = col[0];
                     for (int64_t q = 1; q < base; q++) {
-                        const cplx e = wb[(k * q) % base];
-                        acc.re += e.re * c[q].re - e.im * c[q].im;
-                        acc.im += e.re * c[q].im + e.im * c[q].re;
+                        const cplx f = F[k * base + q];
+                        s.re += f.re * col[q].re - f.im * col[q].im;
+                        s.im += f.re * col[q].im + f.im * col[q].re;
                     }
-                    x[i + j + k * L] = acc;
+                    v[k * L] = s;
                 }
             }
     }
-    memcpy(out, x, sizeof(cplx) * (size_t)n);
-    free(w);
-    free(wb);
-    free(x);
-    free(c);
+    memcpy(out, z, sizeof(cplx) * (size_t)n);
+    free(wn);
+    free(F);
+    free(z);
+    free(col);
     return OR_OK;
 }
 
