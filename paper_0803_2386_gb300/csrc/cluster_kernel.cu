@@ -44,6 +44,7 @@
 
 #include "codelets.cuh"
 #include "internal.h"
+#include "kernel_setup.cuh"
 #include "tcgen05.cuh"
 
 namespace moafft {
@@ -255,72 +256,84 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// the driver entry point is the same for every device: looked up once per
+// process, thread-safely, as a function-local static
 EncodeTiledFn encode_fn()
 {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
+        EncodeTiledFn f = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)ptr;
+            f = (EncodeTiledFn)ptr;
         cudaGetLastError();
-    }
+        return f;
+    }();
     return fn;
 }
 
+// clusters of C CTAs resident at once on the current device (0: none),
+// with the kernel's attributes set; once per device
 template <int DIR, int C>
 int max_clusters()
 {
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    cached = 0;
-    int dev = 0, ok = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev) != cudaSuccess || !ok) return 0;
-    cudaError_t e = cudaFuncSetAttribute(cluster_kernel<DIR, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<C>::smem);
-    if (e == cudaSuccess && C > 8)
-        e = cudaFuncSetAttribute(cluster_kernel<DIR, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) {
+    static DeviceOnce setup;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(Geo<C>::threads, 1, 1);
-    cfg.dynamicSmemBytes = Geo<C>::smem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel<DIR, C>, &cfg) != cudaSuccess) {
-        cudaGetLastError();
+    long long n = 0;
+    device_once(setup, dev, &n, [&](int devno, long long *v) -> int {
+        *v = 0;
+        int ok = 0;
+        if (cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, devno) != cudaSuccess || !ok) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaError_t e = cudaFuncSetAttribute(cluster_kernel<DIR, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Geo<C>::smem);
+        if (e == cudaSuccess && C > 8)
+            e = cudaFuncSetAttribute(cluster_kernel<DIR, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof cfg);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(Geo<C>::threads, 1, 1);
+        cfg.dynamicSmemBytes = Geo<C>::smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int cnt = 0;
+        if (cudaOccupancyMaxActiveClusters(&cnt, cluster_kernel<DIR, C>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        *v = cnt;
         return 0;
-    }
-    cached = n;
-    return n;
+    });
+    return (int)n;
 }
 
-// cluster size: 16 (two CTAs per SM) unless MOAFFT_CLUSTER=8 or the device
-// cannot hold 16-CTA clusters
+// cluster size on the current device: 16 (two CTAs per SM) unless
+// MOAFFT_CLUSTER=8 or the device cannot hold 16-CTA clusters
 int cluster_size()
 {
-    static int c = 0;
-    if (c == 0) {
+    static const bool want8 = [] {
         const char *env = getenv("MOAFFT_CLUSTER");
-        c = (env && atoi(env) == 8) ? 8 : 16;
-        if (c == 16 && (max_clusters<-1, 16>() <= 0 || max_clusters<1, 16>() <= 0)) c = 8;
-    }
-    return c;
+        return env && atoi(env) == 8;
+    }();
+    if (want8) return 8;
+    return (max_clusters<-1, 16>() <= 0 || max_clusters<1, 16>() <= 0) ? 8 : 16;
 }
 
 template <int DIR, int C>

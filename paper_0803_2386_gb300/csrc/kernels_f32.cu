@@ -1,6 +1,7 @@
 // kernels_f32.cu -- instantiations and launcher of the pass kernel for
 // float arithmetic (element type float2).
 #include "pass_kernel.cuh"
+#include "kernel_setup.cuh"
 #include "tile_kernel.cuh"
 
 namespace moafft {
@@ -11,14 +12,9 @@ size_t pass_smem_bytes(const PassArgs &a, size_t elem_bytes);
 template <int DIR>
 static cudaError_t launch_dir_f32(const PassArgs &a, cudaStream_t s)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel<float, DIR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static DeviceOnce setup;
+    cudaError_t e = smem_setup(setup, pass_kernel<float, DIR>, 200 * 1024);
+    if (e != cudaSuccess) return e;
     const int R = 1 << a.log_r;
     int64_t ctas;
     if (!a.is_last) ctas = a.count * a.A * (a.B / a.width);

@@ -1,5 +1,6 @@
 // tc_f32.cu -- instantiations and launcher of the tensor-core tile kernel
 // (complex64, radix-16 digits as split FP16/BF16 products).
+#include "kernel_setup.cuh"
 #include "tc_tile_kernel.cuh"
 
 namespace moafft {
@@ -9,17 +10,9 @@ static cudaError_t launch_tc_one(const PassArgs &a, cudaStream_t s)
 {
     constexpr int W = tile_width(LOGR);
     constexpr size_t smem = tc_smem_bytes<DIR, LOGR>();
-    static bool init = false;
-    if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(tc_tile_kernel<DIR, LOGR, LAST, BF16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tc_tile_kernel<DIR, LOGR, LAST, BF16>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        init = true;
-    }
+    static DeviceOnce setup;
+    cudaError_t e = smem_setup(setup, tc_tile_kernel<DIR, LOGR, LAST, BF16>, smem);
+    if (e != cudaSuccess) return e;
     int64_t ctas;
     if (!LAST) ctas = a.count * a.A * (a.B / W);
     else if (a.A > 1) ctas = a.count * (a.A / W);

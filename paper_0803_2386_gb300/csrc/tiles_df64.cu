@@ -1,5 +1,6 @@
 // tiles_df64.cu -- instantiations and launcher of the tile kernel in
 // double-float arithmetic (complex128 in HBM, FP32 pipes for the math).
+#include "kernel_setup.cuh"
 #include "tile_kernel.cuh"
 
 namespace moafft {
@@ -9,17 +10,9 @@ static cudaError_t launch_df_one(const PassArgs &a, cudaStream_t s)
 {
     constexpr int W = tile_width(LOGR);
     constexpr size_t smem = LOGR >= 5 ? (size_t)((1 << LOGR) + (1 << LOGR) / 16) * W * sizeof(dcplx) : 0;
-    static bool init = false;
-    if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<dfloat, DIR, LOGR, LAST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tile_kernel<dfloat, DIR, LOGR, LAST>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        init = true;
-    }
+    static DeviceOnce setup;
+    cudaError_t e = smem_setup(setup, tile_kernel<dfloat, DIR, LOGR, LAST>, smem);
+    if (e != cudaSuccess) return e;
     int64_t ctas;
     if (!LAST) ctas = a.count * a.A * (a.B / W);
     else if (a.A > 1) ctas = a.count * (a.A / W);
