@@ -58,6 +58,12 @@ typedef enum { FFT_FORWARD = -1, FFT_INVERSE = 1 } fft_dir;
  *   arithmetic -- each double carried as an unevaluated sum of two floats
  *   (about 48 significant bits) computed on the FP32 pipes, with complex128
  *   kept as the memory format; relative error of a few 1e-15 per operation.
+ *   Range: both floats use FP32's exponent, so the precision holds while
+ *   every input, output and partial sum lies between about 2e-31 (below it
+ *   the low float is an FP32 subnormal and the result degrades towards
+ *   single precision; below 1.4e-45 a value flushes to zero) and 3.4e38
+ *   (beyond it a value becomes infinite; outputs reach n times the largest
+ *   input).  The data are not checked.
  *   Needs every pass to be a tile of 2^4..2^12 points (the default
  *   schedules are); FFT_ERR_UNSUPPORTED otherwise. */
 typedef enum {
@@ -182,24 +188,53 @@ int fft_exec_host(fft_plan_t p, const void *in, void *out, void *cuda_stream);
  * else -- the weight tables and the buffer that carries the data between
  * HBM passes -- in one fixed 32 MiB __device__ array inside the library,
  * which every GPU that loads the library holds until the process exits.
+ * It runs the pass split and tile kernels a plan of length n uses by default
+ * (not the narrow two-pass schedule fft_plan picks for a few small
+ * complex128 transforms), with two-level pass-weight tables.
  * Limit: complex128 n <= 2^20, complex64 n <= 2^21 (any batch; larger n is
  * rejected with FFT_ERR_UNSUPPORTED and a message, before any GPU work).
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
- * call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  Every call shares the one array and leaves its
- * contents behind; nothing in it needs to start at zero, because each call
- * writes every table entry and workspace element before reading it.  Calls
- * whose GPU work overlaps (for instance on two streams) race on the array
- * and give wrong results: serialise them.  Asynchronous like fft_exec. */
+ * call on a device looks up the device addresses of the array and of its
+ * error word with cudaGetSymbolAddress (with that device current); make that
+ * first call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind; nothing in it needs to start at zero, because
+ * each call writes every table entry and workspace element before reading
+ * it.  Calls whose GPU work overlaps (for instance on two streams) race on
+ * the array and give wrong results: serialise them.  Asynchronous like
+ * fft_exec; a bounded device-side wait that gave up is reported by
+ * fft_noalloc_check. */
 int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t batch, fft_dtype dt,
                      fft_dir dir, void *cuda_stream);
+
+/* Synchronise the current device and report what the kernels of
+ * fft_exec_noalloc recorded since the last check: FFT_ERR_TIMEOUT if one of
+ * their bounded device-side waits (the TMA-staged complex64 passes' mbarrier
+ * waits) gave up (the flag, a word beside the fixed array, is then
+ * cleared), FFT_ERR_CUDA if the device reports an error, else FFT_OK.
+ * Allocates nothing.  (No counterpart in the paper: the status query of the
+ * allocation-free entry point.) */
+int fft_noalloc_check(void);
 
 /* Synchronise the device and report what the plan's kernels recorded:
  * FFT_ERR_TIMEOUT if a bounded device-side wait (the tensor-core form's
  * mbarrier waits) gave up since the last check (the flag is then cleared),
  * FFT_ERR_CUDA if the device reports an error, else FFT_OK. */
 int fft_plan_check(fft_plan_t p);
+
+/* The bounded waits of an uneven plan's persistent launch (fft_plan_many
+ * with MOAFFT_PERSIST=1): every tile of a second pass first waits until the
+ * first-pass tiles of its workspace round have signalled a counter.  Such a
+ * wait polls for at most limit_cycles SM clock cycles (default 2e9, about a
+ * second at 2 GHz), then records FFT_ERR_TIMEOUT for fft_plan_check, skips
+ * its tile and lets the kernel finish.  target_offset (>= 0, default 0) is
+ * added to every wait's target: a nonzero offset asks for more tiles than
+ * exist, so every such wait runs out -- a way to test failure detection
+ * without faulting or hanging the GPU.  Synchronises the device; the next
+ * execution captures the plan's graph again.  FFT_ERR_UNSUPPORTED for plans
+ * without a persistent launch, FFT_ERR_ARG for limit_cycles < 1 or a
+ * negative offset.  (No counterpart in the paper: failure detection of the
+ * batching form.) */
+int fft_plan_set_wait(fft_plan_t p, int64_t limit_cycles, int32_t target_offset);
 
 /* Release everything the plan owns.  NULL is a no-op.  Synchronises the
  * device before freeing. */

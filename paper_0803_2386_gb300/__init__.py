@@ -41,7 +41,7 @@ STATUS_NAMES = {0: "FFT_OK", -1: "FFT_ERR_ARG", -2: "FFT_ERR_NOT_POW2", -3: "FFT
 
 # every symbol include/moafft.h declares
 EXPORTS = ["fft_plan", "fft_plan_ex", "fft_plan_many", "fft_plan_nd", "fft_exec", "fft_exec_adjoint",
-           "fft_exec_host", "fft_exec_noalloc", "fft_plan_check", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
+           "fft_exec_host", "fft_exec_noalloc", "fft_noalloc_check", "fft_plan_check", "fft_plan_set_wait", "fft_plan_profile", "fft_plan_pass_times", "fft_destroy", "fft_last_error", "fft_describe_schedule", "fft_plan_describe",
            "fft_plan_launches", "fft_plan_workspace_bytes", "fft_set_allocator", "fft_tune_candidates", "fft_version",
            "dm_gate", "dm_transpose_vector"]
 
@@ -82,7 +82,9 @@ def lib():
             "fft_exec_adjoint": (i32, [vp, vp, vp, vp]),
             "fft_exec_host": (i32, [vp, vp, vp, vp]),
             "fft_exec_noalloc": (i32, [vp, vp, i64, i64, i32, i32, vp]),
+            "fft_noalloc_check": (i32, []),
             "fft_plan_check": (i32, [vp]),
+            "fft_plan_set_wait": (i32, [vp, i64, ctypes.c_int32]),
             "fft_plan_profile": (i32, [vp, i32]),
             "fft_plan_pass_times": (i32, [vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(i64), i32]),
@@ -201,6 +203,12 @@ def fft_exec_noalloc(inp, out, n: int, batch: int, dtype: int, direction: int = 
                                   _stream(stream, inp, out)))
 
 
+def fft_noalloc_check():
+    """Synchronise the current device; raise if a bounded wait of an
+    fft_exec_noalloc kernel gave up since the last check (then cleared)."""
+    _check(lib().fft_noalloc_check())
+
+
 def _int_array(values):
     arr = (ctypes.c_int * max(1, len(values)))(*[int(v) for v in values])
     return arr
@@ -232,6 +240,13 @@ def dm_gate(rho, qubits, u, stream=None):
 def fft_plan_check(plan: int):
     """Synchronise; raise on a recorded device-side timeout or CUDA error."""
     _check(lib().fft_plan_check(plan))
+
+
+def fft_plan_set_wait(plan: int, limit_cycles: int = 2000000000, target_offset: int = 0):
+    """Bounded waits of a persistent uneven plan: the poll limit in SM
+    cycles, and an offset added to every wait's target (nonzero makes every
+    wait run out: failure-detection tests)."""
+    _check(lib().fft_plan_set_wait(plan, int(limit_cycles), int(target_offset)))
 
 
 def fft_plan_profile(plan: int, enable: bool = True):

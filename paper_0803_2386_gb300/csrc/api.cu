@@ -226,6 +226,12 @@ static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
     return finish_schedule(s, dt, nullptr);
 }
 
+namespace moafft {
+// the default pass split and tile widths of a plan of length n (used by the
+// allocation-free entry point, noalloc.cu)
+int default_pass_schedule(Schedule &s, int64_t n, fft_dtype dt) { return default_schedule(s, n, dt); }
+}  // namespace moafft
+
 // "r0[@w0][/k0],r1[@w1][/k1],...": radix 2^r per pass, tile width w, register
 // digits of at most 2^k points (k = 1..4; default 4)
 static int parse_schedule(Schedule &s, int64_t n, fft_dtype dt, const char *text)
@@ -508,6 +514,12 @@ struct fft_plan_s {
     bool persist = false;
     std::vector<int64_t> ws_off;  // per class: element offset of its workspace
     int n_ctr = 0;
+    // the persistent kernel's waits on round counters: clock64 cycles a wait
+    // polls before it gives up (about one second at 2 GHz), and an offset
+    // added to every wait's target (fft_plan_set_wait; nonzero only to test
+    // failure detection: a target no tile will reach)
+    long long wait_limit = 2000000000LL;
+    int wait_offset = 0;
     DevBuf d_segs, d_queue, d_ctr;
     cudaStream_t s_capture = nullptr;
     // a second captured branch: the single-pass classes (which need no
@@ -779,9 +791,12 @@ static int finish_plan(fft_plan_s *p, int64_t req_chunk)
     e = cudaMemset(p->err.ptr, 0, sizeof(int));
     if (e != cudaSuccess) return fail_cuda(e, "error word");
     if (p->form != FFT_FORM_PLAIN) {
-        st = dev_alloc(p->tcf, 8192, "tensor-core DFT matrices");
+        // split DFT matrices for both directions: 16-point (8 KiB), then
+        // 32-point (32 KiB)
+        st = dev_alloc(p->tcf, 8192 + 32768, "tensor-core DFT matrices");
         if (st != FFT_OK) return st;
         e = launch_tc_tables(p->tcf.ptr, p->form == FFT_FORM_TC_BF16, 0);
+        if (e == cudaSuccess) e = launch_tcf_tables((char *)p->tcf.ptr + 8192, 5, p->form == FFT_FORM_TC_BF16, 0);
         if (e != cudaSuccess) return fail_cuda(e, "tensor-core DFT matrices");
     }
     return make_tables(p);
@@ -1129,7 +1144,8 @@ static void build_segments(const fft_plan_s *p, const void *in, void *out, std::
                 a.in = ws;
                 a.out = out;
                 a.out_off = off;
-                add(a, c.sched.pass[1], cnt, ctr + (int)j, (int)pass_ctas(c.sched.pass[0], cnt), -1);
+                add(a, c.sched.pass[1], cnt, ctr + (int)j, (int)pass_ctas(c.sched.pass[0], cnt) + p->wait_offset,
+                    -1);
             }
         };
         round(0, 0);
@@ -1306,6 +1322,7 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.scale = a.is_last ? scale : 1.0;
             a.err = (int *)p->err.ptr;
             a.tc_dft = p->tcf.ptr ? (const char *)p->tcf.ptr + (sign < 0 ? 0 : 4096) : nullptr;
+            a.tc_dft32 = p->tcf.ptr ? (const char *)p->tcf.ptr + 8192 + (sign < 0 ? 0 : 16384) : nullptr;
             fft_plan_s::Rec rec{i, nullptr, nullptr};
             if (p->profile) {
                 rec.a = take_event(p);
@@ -1315,8 +1332,13 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             cudaError_t e;
             if (p->form == FFT_FORM_DF64) e = launch_tile_df64(a, sign, s);
             else if (p->dt == FFT_C128) e = launch_pass_f64(a, sign, s);
-            else if (p->form != FFT_FORM_PLAIN && tc_covers(a))
-                e = launch_tc_f32(a, sign, p->form == FFT_FORM_TC_BF16, s);
+            else if (p->form != FFT_FORM_PLAIN && (tcf_covers(a) || tc_covers(a))) {
+                e = launch_tcf_f32(a, sign, p->form == FFT_FORM_TC_BF16, s);
+                if (e == cudaErrorNotSupported) {
+                    cudaGetLastError();
+                    e = tc_covers(a) ? launch_tc_f32(a, sign, p->form == FFT_FORM_TC_BF16, s) : launch_pass_f32(a, sign, s);
+                }
+            }
             else e = launch_pass_f32(a, sign, s);
             if (e != cudaSuccess) return fail_cuda(e, "pass launch");
             if (p->profile && rec.a && rec.b) {
@@ -1444,8 +1466,8 @@ static int exec_graph(fft_plan_t p, const void *in, void *out, int sign, cudaStr
             if (e2 == cudaSuccess) {
                 auto fn = p->dt == FFT_C128 ? launch_persist_f64 : launch_persist_f32;
                 e2 = fn((const PersistSeg *)p->d_segs.ptr, (int)segs.size(), total,
-                        (unsigned long long *)p->d_queue.ptr, (int *)p->d_ctr.ptr, (int *)p->err.ptr, sign,
-                        p->s_capture);
+                        (unsigned long long *)p->d_queue.ptr, (int *)p->d_ctr.ptr, (int *)p->err.ptr,
+                        p->wait_limit, sign, p->s_capture);
             }
             if (e2 != cudaSuccess) st = fail_cuda(e2, "persistent launch");
         } else {
@@ -1659,6 +1681,23 @@ extern "C" int fft_plan_check(fft_plan_t p)
     if (flag) {
         cudaMemset(p->err.ptr, 0, sizeof(int));
         return fail(FFT_ERR_TIMEOUT, "a bounded device-side wait of this plan's kernels gave up");
+    }
+    return FFT_OK;
+}
+
+extern "C" int fft_plan_set_wait(fft_plan_t p, int64_t limit_cycles, int32_t target_offset)
+{
+    if (!p) return fail(FFT_ERR_ARG, "plan is NULL");
+    if (limit_cycles < 1) return fail(FFT_ERR_ARG, "wait limit %lld < 1 cycle", (long long)limit_cycles);
+    if (target_offset < 0) return fail(FFT_ERR_ARG, "wait target offset %d < 0", (int)target_offset);
+    if (!p->persist) return fail(FFT_ERR_UNSUPPORTED, "the plan has no persistent launch (its waits are fixed)");
+    cudaError_t e = cudaDeviceSynchronize();  // no replay of the old graph is in flight
+    if (e != cudaSuccess) return fail_cuda(e, "fft_plan_set_wait (sync)");
+    p->wait_limit = limit_cycles;
+    p->wait_offset = target_offset;
+    if (p->gexec) {  // captured with the old values: capture again on the next execution
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
     }
     return FFT_OK;
 }

@@ -28,6 +28,13 @@ namespace moafft {
 
 constexpr uint32_t kBulkWaitPolls = 1u << 22;
 
+// The tensor map of a complex64 column pass (tiles_f32.cu): the signal as
+// rows of B points, boxes of W columns by min(R, 256) rows; false when the
+// buffers do not allow one.
+bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map);
+// A tensor map over a row-major table of complex64 entries (tiles_f32.cu).
+bool table_tensor_map(const void *base, int64_t cols, int64_t rows, int box_cols, int box_rows, CUtensorMap *map);
+
 // column tiles need 16-byte box rows (W * 8 >= 16 for complex64); row
 // tiles are whole rows of up to 2^12 points
 __host__ __device__ constexpr bool bulk_ok(int logr, bool last) { return logr >= 4 && logr <= (last ? 12 : 11); }

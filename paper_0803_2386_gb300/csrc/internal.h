@@ -113,8 +113,10 @@ struct PassArgs {
     // device word set to 1 when a bounded wait inside a kernel gave up
     int *err;
     // tensor-core form: the split 32x32 DFT matrix of this direction, hi
-    // then lo, 2 x 2048 bytes in the K-major core-matrix layout
+    // then lo, 2 x 2048 bytes in the K-major core-matrix layout, and the
+    // same for the 32-point DFT (64x64 reals, 2 x 8192 bytes)
     const void *tc_dft;
+    const void *tc_dft32;
 };
 
 // One segment of a persistent launch: tickets [first, first + nctas) are the
@@ -133,10 +135,12 @@ struct PersistSeg {
 };
 
 // persistent uneven-batch launchers (persist_f32.cu / persist_f64.cu)
+// limit_cycles: clock64 cycles a tile's wait on a round counter polls
+// before it gives up (records a timeout in *err and skips the tile)
 cudaError_t launch_persist_f32(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
-                               int *counters, int *err, int dir, cudaStream_t s);
+                               int *counters, int *err, long long limit_cycles, int dir, cudaStream_t s);
 cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
-                               int *counters, int *err, int dir, cudaStream_t s);
+                               int *counters, int *err, long long limit_cycles, int dir, cudaStream_t s);
 
 // unblocked per-stage transform (stages.cu); tmp (n * count elements) is
 // used when in == out
@@ -166,6 +170,14 @@ bool tc_covers(const PassArgs &a);
 // 4096 bytes each, into dst (tc_f32.cu)
 cudaError_t launch_tc_tables(void *dst, bool bf16, cudaStream_t s);
 cudaError_t launch_tc_f32(const PassArgs &a, int dir, bool bf16, cudaStream_t s);
+// tensor-core passes of 2^8 = 16 x 16 and 2^10 = 32 x 32 points with both
+// DFT digits as tcgen05 products, persistent and TMA-staged (tcf_f32.cu);
+// cudaErrorNotSupported when the pass is not one they cover
+bool tcf_covers(const PassArgs &a);
+cudaError_t launch_tcf_f32(const PassArgs &a, int dir, bool bf16, cudaStream_t s);
+// the split 32-point DFT matrices for both directions (dir -1 first), 16384
+// bytes each (hi then lo), into dst
+cudaError_t launch_tcf_tables(void *dst, int logd, bool bf16, cudaStream_t s);
 
 // twiddle generation (twiddle.cu): dst[j] = exp(-2*pi*i * j*stride / m),
 // j < count, computed in FP64 with sincospi; f32 variant rounds once.
@@ -204,6 +216,10 @@ cudaError_t launch_digit_tables(void *dst, int kind, int log_r, cudaStream_t s);
 // of 2^4..2^12 points with the tile kernel's widths
 bool df64_covers(const PassArgs &a);
 cudaError_t launch_tile_df64(const PassArgs &a, int dir, cudaStream_t s);
+
+// the default pass split and tile widths of a plan of length n (api.cu);
+// FFT_OK or a negative fft_status
+int default_pass_schedule(Schedule &s, int64_t n, fft_dtype dt);
 
 // threads per CTA for a pass
 int pass_threads(const PassArgs &a);

@@ -13,9 +13,13 @@
 // when the library's module is loaded and held by every GPU that loads the
 // library until the process exits.
 //
-// It runs the same pass kernels as fft_exec, with the default pass
-// schedule, but always with two-level weight tables (two tables of about
-// sqrt(M) entries each) so that the tables stay small.
+// It runs the same pass kernels as fft_exec with the default pass split and
+// tile widths of a plan of the same length (the narrow-tile latency
+// schedule fft_plan picks for a few small complex128 transforms is not
+// used), but with two-level pass-weight tables (two tables of about sqrt(M)
+// entries each) so that the tables stay small.  A kernel whose bounded wait
+// gives up records it in a file-scope device word beside the array;
+// fft_noalloc_check reads and clears it.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -33,10 +37,13 @@ using namespace moafft;
 #define MOAFFT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MOAFFT_NOALLOC_SCRATCH_BYTES];
+// set to 1 by a kernel of this entry point whose bounded wait gave up
+static __device__ int g_noalloc_err_word;
 
 static thread_local char g_noalloc_err[256];
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[128];  // device address of the array, per device ordinal
+static int *g_noalloc_errp[128];  // device address of the error word, per device ordinal
 
 // fft_last_error() lives in api.cu; this file keeps its own message buffer
 // and exposes it through the same function by forwarding the text.
@@ -60,10 +67,11 @@ static int ilog2(int64_t n)
     return t;
 }
 
-// Set-up, once per device and with that device current: the address of the
-// array on this device.  In host code the array's name is only a host-side
-// stand-in, so the device address must come from cudaGetSymbolAddress.
-static int scratch_address(void **out)
+// Set-up, once per device and with that device current: the addresses of
+// the array and of the error word on this device.  In host code their names
+// are only host-side stand-ins, so the device addresses must come from
+// cudaGetSymbolAddress.
+static int scratch_address(void **out, int **err)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -74,15 +82,18 @@ static int scratch_address(void **out)
     if (dev < 0 || dev >= 128) return nfail(FFT_ERR_UNSUPPORTED, "fft_exec_noalloc: device ordinal%s %lld >= 128", "", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
+        void *p = nullptr, *q = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_err_word);
+        if (e != cudaSuccess || !p || !q) {
             cudaGetLastError();
             return nfail(FFT_ERR_CUDA, "fft_exec_noalloc: cudaGetSymbolAddress failed (%s)", cudaGetErrorName(e));
         }
+        g_noalloc_errp[dev] = (int *)q;
         g_noalloc_ptr[dev] = p;
     }
     *out = g_noalloc_ptr[dev];
+    if (err) *err = g_noalloc_errp[dev];
     return FFT_OK;
 }
 
@@ -110,39 +121,30 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
     if (n < 1 || batch < 1) return nfail(FFT_ERR_ARG, "fft_exec_noalloc: n%s = %lld, batch = %lld", "", n, batch);
     const int t = ilog2(n);
     if (t < 0) return nfail(FFT_ERR_NOT_POW2, "fft_exec_noalloc: n%s = %lld is not a power of two", "", n);
+    if (t > 30)
+        return nfail(FFT_ERR_UNSUPPORTED,
+                     "fft_exec_noalloc: n%s = %lld is beyond the fixed 32 MiB array (complex128 n <= 2^20, complex64 "
+                     "n <= 2^21)", "", n);
     const size_t eb = dt == FFT_C128 ? 16 : 8;
 
-    // default schedule: passes of at most 2^11, radices as even as possible
+    // the plan's default pass split and tile widths; the pass weights in
+    // two-level tables (w_M^e for e < 2^lo and for multiples of 2^lo), which
+    // the tile kernels read as well as the plan's larger row tables
     Schedule S;
-    S.n = n;
-    S.t = t;
-    const int mt = 11;
-    const int g = t == 0 ? 1 : (t + mt - 1) / mt;
-    if (g > kMaxPasses) return nfail(FFT_ERR_UNSUPPORTED, "fft_exec_noalloc: n%s = 2^%lld is too large", "", t);
-    S.npass = g;
-    const int64_t budget = dt == FFT_C128 ? 4096 : 8192;
-    int64_t A = 1;
+    int st = default_pass_schedule(S, n, dt);
+    if (st != FFT_OK) return st;
+    const int g = S.npass;
     size_t tables = 0;  // elements
     for (int i = 0; i < g; i++) {
         PassDesc &p = S.pass[i];
-        p.log_r = t / g + (i < t % g ? 1 : 0);
         const int64_t R = (int64_t)1 << p.log_r;
-        p.A = A;
-        p.B = n / (A * R);
-        A *= R;
         const bool last = (i == g - 1);
-        int64_t w = std::max<int64_t>(1, budget / R);
-        w = std::min<int64_t>(w, last && p.A == 1 ? 1024 : 16);
-        w = std::min<int64_t>(w, last ? (p.A > 1 ? p.A : w) : p.B);
-        p.width = (int)w;
-        p.nsub = 0;
-        if (p.log_r % 4) p.sub_log[p.nsub++] = p.log_r % 4;
-        for (int k = 0; k < p.log_r / 4; k++) p.sub_log[p.nsub++] = 4;
-        p.tw_m = R * p.B;
         p.tw_tile_off = tables;
         tables += (size_t)R;
         p.tw_digit_off = tables;
         tables += (size_t)digit_table_entries(p.log_r);
+        p.tw_mode = 0;
+        p.tw_lo_bits = 0;
         if (!last) {
             const int lm = ilog2(p.tw_m);
             p.tw_lo_bits = std::max(1, (lm + 1) / 2);
@@ -162,7 +164,7 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
         chunk = std::min<int64_t>(batch, (int64_t)((MOAFFT_NOALLOC_SCRATCH_BYTES - table_bytes) / ((size_t)n * eb)));
     }
 
-    int st = check_dev(in, eb, "in");
+    st = check_dev(in, eb, "in");
     if (st == FFT_OK) st = check_dev(out, eb, "out");
     if (st != FFT_OK) return st;
     const size_t bytes = (size_t)n * (size_t)batch * eb;
@@ -171,7 +173,8 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
         return nfail(FFT_ERR_ALIAS, "fft_exec_noalloc: in and out overlap without being identical%s", "");
 
     void *scratch = nullptr;
-    st = scratch_address(&scratch);
+    int *errw = nullptr;
+    st = scratch_address(&scratch, &errw);
     if (st != FFT_OK) return st;
     char *tw = (char *)scratch;
     char *ws = tw + table_bytes;
@@ -226,11 +229,29 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
             a.tw_pass = tw + p.tw_pass_off * eb;
             a.tw_hi = tw + p.tw_hi_off * eb;
             a.tw_lo_bits = p.tw_lo_bits;
+            a.tw_mode = p.tw_mode;
             a.scale = a.is_last ? scale : 1.0;
+            a.err = errw;
             cudaError_t e = dt == FFT_C128 ? launch_pass_f64(a, sign, s) : launch_pass_f32(a, sign, s);
             if (e != cudaSuccess)
                 return nfail(FFT_ERR_CUDA, "fft_exec_noalloc: pass launch failed (%s)", cudaGetErrorName(e));
         }
     }
+    return FFT_OK;
+}
+
+extern "C" int fft_noalloc_check(void)
+{
+    void *scratch = nullptr;
+    int *errw = nullptr;
+    int st = scratch_address(&scratch, &errw);
+    if (st != FFT_OK) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return nfail(FFT_ERR_CUDA, "fft_noalloc_check: %s", cudaGetErrorName(e));
+    int h = 0;
+    e = cudaMemcpy(&h, errw, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(errw, 0, sizeof h);
+    if (e != cudaSuccess) return nfail(FFT_ERR_CUDA, "fft_noalloc_check: %s", cudaGetErrorName(e));
+    if (h) return nfail(FFT_ERR_TIMEOUT, "fft_exec_noalloc: a bounded device-side wait gave up%s", "");
     return FFT_OK;
 }

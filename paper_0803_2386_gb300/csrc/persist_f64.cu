@@ -1,40 +1,29 @@
 // persist_f64.cu -- the persistent uneven-batch kernel for double arithmetic.
+#include "kernel_setup.cuh"
 #include "persist_kernel.cuh"
 
 namespace moafft {
 
 template <int DIR>
 static cudaError_t launch_persist_dir(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
-                                      int *counters, int *err, cudaStream_t s)
+                                      int *counters, int *err, long long limit, cudaStream_t s)
 {
     using V = typename cvec<double>::type;
     constexpr size_t smem = (size_t)(4096 + 256) * sizeof(V);
-    static int grid = 0;
-    if (grid == 0) {
-        cudaError_t e = cudaFuncSetAttribute(persist_kernel<double, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(persist_kernel<double, DIR>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        int dev = 0, sms = 0, per = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_kernel<double, DIR>, kPersistThreads, smem);
-        if (e != cudaSuccess) return e;
-        grid = sms * (per > 0 ? per : 1);
-    }
-    // about one second of spinning at most before a wait is declared lost
-    const long long limit = 2000000000LL;
+    static DeviceOnce setup;
+    int grid = 0;
+    cudaError_t e = persistent_grid(setup, persist_kernel<double, DIR>, kPersistThreads, smem, &grid);
+    if (e != cudaSuccess) return e;
     persist_kernel<double, DIR><<<grid, kPersistThreads, smem, s>>>(segs, nseg, total, queue, counters, err, limit);
     return cudaGetLastError();
 }
 
 cudaError_t launch_persist_f64(const PersistSeg *segs, int nseg, long long total, unsigned long long *queue,
-                               int *counters, int *err, int dir, cudaStream_t s)
+                               int *counters, int *err, long long limit_cycles, int dir, cudaStream_t s)
 {
-    return dir < 0 ? launch_persist_dir<-1>(segs, nseg, total, queue, counters, err, s)
-                   : launch_persist_dir<1>(segs, nseg, total, queue, counters, err, s);
+    if (limit_cycles < 1) limit_cycles = 1;
+    return dir < 0 ? launch_persist_dir<-1>(segs, nseg, total, queue, counters, err, limit_cycles, s)
+                   : launch_persist_dir<1>(segs, nseg, total, queue, counters, err, limit_cycles, s);
 }
 
 }  // namespace moafft

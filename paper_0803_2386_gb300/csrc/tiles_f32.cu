@@ -1,6 +1,7 @@
 // tiles_f32.cu -- instantiations and launcher of the compile-time-radix
 // tile kernel for float arithmetic (tiles of 2^4 .. 2^12 points).
 #include "bulk_kernel.cuh"
+#include "kernel_setup.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -15,17 +16,9 @@ static cudaError_t launch_tile_one(const PassArgs &a, cudaStream_t s)
     using V = typename cvec<float>::type;
     constexpr int W = tile_width(LOGR);
     constexpr size_t smem = LOGR >= 5 ? (size_t)((1 << LOGR) + (1 << LOGR) / 16) * W * sizeof(V) : 0;
-    static bool init = false;
-    if (!init) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<float, DIR, LOGR, LAST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tile_kernel<float, DIR, LOGR, LAST>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        init = true;
-    }
+    static DeviceOnce setup;
+    cudaError_t e = smem_setup(setup, tile_kernel<float, DIR, LOGR, LAST>, smem);
+    if (e != cudaSuccess) return e;
     int64_t ctas;
     if (!LAST) ctas = a.count * a.A * (a.B / W);
     else if (a.A > 1) ctas = a.count * (a.A / W);
@@ -43,26 +36,27 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // cuTensorMapEncodeTiled, reached through the runtime (no link to libcuda)
+// (the driver entry point is the same for every device; the look-up runs
+// once per process, thread-safely, as a function-local static)
 static EncodeTiledFn encode_fn()
 {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
+        EncodeTiledFn f = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)ptr;
+            f = (EncodeTiledFn)ptr;
         cudaGetLastError();
-    }
+        return f;
+    }();
     return fn;
 }
 
 // The tensor map of a column pass: rows of B points (8 bytes each), one row
 // per (transform, a, m); boxes of W columns by min(R, 256) rows.
-static bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map)
+bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -80,34 +74,38 @@ static bool column_tensor_map(const PassArgs &a, int W, CUtensorMap *map)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// A 2-D tensor map over a row-major table of `rows` rows of `cols` complex64
+// entries, boxes of box_cols x box_rows; false when the table's address or
+// row pitch is not 16-byte aligned or the encoding fails.
+bool table_tensor_map(const void *base, int64_t cols, int64_t rows, int box_cols, int box_rows, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || ((uintptr_t)base % 16) != 0 || (cols * 8) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 8};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // persistent form with TMA-staged loads (bulk_kernel.cuh)
 template <int DIR, int LOGR, bool LAST>
 static cudaError_t launch_bulk_one(const PassArgs &a, cudaStream_t s)
 {
     constexpr int W = tile_width(LOGR);
     constexpr size_t smem = bulk_smem_bytes<LOGR, LAST>();
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(bulk_kernel<DIR, LOGR, LAST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(bulk_kernel<DIR, LOGR, LAST>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        int dev = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bulk_kernel<DIR, LOGR, LAST>,
-                                                              tile_threads(LOGR), smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
+    static DeviceOnce setup;
+    int resident = 0;  // SMs x CTAs per SM on this device
+    cudaError_t e = persistent_grid(setup, bulk_kernel<DIR, LOGR, LAST>, tile_threads(LOGR), smem, &resident);
+    if (e != cudaSuccess) return e;
     int64_t ctas;
     if (!LAST) ctas = a.count * a.A * (a.B / W);
     else if (a.A > 1) ctas = a.count * (a.A / W);
     else ctas = (a.count + W - 1) / W;
     if (ctas <= 0) return cudaSuccess;
-    const int64_t grid = std::min<int64_t>(ctas, (int64_t)sms * per_sm);
+    const int64_t grid = std::min<int64_t>(ctas, (int64_t)resident);
     CUtensorMap map;
     memset(&map, 0, sizeof map);
     if (!LAST && !column_tensor_map(a, W, &map)) return cudaErrorNotSupported;

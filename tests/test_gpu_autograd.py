@@ -12,6 +12,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_one, err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -93,5 +94,5 @@ def test_gradient_vs_oracle_adjoint(problem):
     G = 2.0 * np.conj(Hs) * (X * Hs - ys)  # grad w.r.t. X in PyTorch's convention
     ref = O.fft(G, "adjoint_forward", c=1024, threads=3)
     got = g[picks].cpu().numpy().astype(np.complex128)
-    err = np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    err = err_rows(got, ref)
     assert err.max() <= 2e-6 * 18, err

@@ -10,6 +10,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -26,9 +27,6 @@ def gpu():
     M.build()
     yield
 
-
-def rel_rows(a, b):
-    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
 
 
 def run(x, direction=M.FFT_FORWARD, schedule=None, adjoint=False, inplace=False, offset=0):
@@ -60,7 +58,7 @@ def test_cluster_plan_is_one_launch():
     y, desc = run(x, schedule="cluster")
     assert desc["schedule"]["cluster"] is True and desc["launches"] == 1
     assert desc["cluster_ctas"] in (8, 16) and desc["resident_clusters"] >= 1
-    assert rel_rows(y, ref(x, "forward")).max() <= TOL
+    assert err_rows(y, ref(x, "forward")).max() <= TOL
 
 
 @pytest.mark.parametrize("batch", [1, 3, 41])
@@ -71,17 +69,17 @@ def test_cluster_parity(batch, direction):
     x = W.uniform_complex(N, batch, seed=300 + batch)
     y, _ = run(x, direction, schedule="cluster")
     op = "forward" if direction == M.FFT_FORWARD else "inverse"
-    assert rel_rows(y, ref(x, op)).max() <= TOL
+    assert err_rows(y, ref(x, op)).max() <= TOL
 
 
 def test_cluster_adjoint_and_in_place():
     x = W.uniform_complex(N, 5, seed=21)
     y, _ = run(x, M.FFT_FORWARD, schedule="cluster", adjoint=True)
-    assert rel_rows(y, ref(x, "adjoint_forward")).max() <= TOL
+    assert err_rows(y, ref(x, "adjoint_forward")).max() <= TOL
     y, _ = run(x, M.FFT_INVERSE, schedule="cluster", adjoint=True)
-    assert rel_rows(y, ref(x, "adjoint_inverse")).max() <= TOL
+    assert err_rows(y, ref(x, "adjoint_inverse")).max() <= TOL
     y, _ = run(x, M.FFT_FORWARD, schedule="cluster", inplace=True)
-    assert rel_rows(y, ref(x, "forward")).max() <= TOL
+    assert err_rows(y, ref(x, "forward")).max() <= TOL
 
 
 def test_cluster_many_rounds_sampled():
@@ -92,7 +90,7 @@ def test_cluster_many_rounds_sampled():
     x = W.gaussian_complex(N, batch, seed=5)
     y, _ = run(x, schedule="cluster")
     rows = [0, 1, 17, 18, 19, 150, 298, 299]
-    assert rel_rows(y[rows], ref(x, "forward", rows)).max() <= TOL
+    assert err_rows(y[rows], ref(x, "forward", rows)).max() <= TOL
     xr = x.astype(np.complex64).astype(np.complex128)
     ex = np.sum(np.abs(xr) ** 2, axis=-1)
     ey = np.sum(np.abs(y) ** 2, axis=-1)
@@ -105,7 +103,7 @@ def test_misaligned_buffer_takes_two_pass_path():
     x = W.uniform_complex(N, 3, seed=8)
     y, desc = run(x, schedule="cluster", offset=1)
     assert desc["schedule"]["cluster"] is True
-    assert rel_rows(y, ref(x, "forward")).max() <= TOL
+    assert err_rows(y, ref(x, "forward")).max() <= TOL
 
 
 def test_cluster_matches_two_pass():
@@ -113,7 +111,7 @@ def test_cluster_matches_two_pass():
     a, _ = run(x, schedule="cluster")
     b, desc = run(x, schedule="8,8")
     assert "cluster" not in desc["schedule"]
-    assert rel_rows(a, b).max() <= 1e-6
+    assert err_rows(a, b).max() <= 1e-6
 
 
 def test_eight_cta_clusters_in_a_child_process():

@@ -8,6 +8,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -21,9 +22,6 @@ def gpu():
     M.build()
     yield
 
-
-def rel_rows(a, b):
-    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
 
 
 def run(x, direction=M.FFT_FORWARD, adjoint=False, inplace=False, rows=None):
@@ -46,11 +44,11 @@ def test_df64_sizes(t):
     n = 1 << t
     x = W.uniform_complex(n, 3, seed=300 + t)
     for direction, op in ((M.FFT_FORWARD, "forward"), (M.FFT_INVERSE, "inverse")):
-        err = rel_rows(run(x, direction), O.fft(x, op, c=64))
+        err = err_rows(run(x, direction), O.fft(x, op, c=64))
         assert err.max() <= 1e-12, (t, op, err.max())
-    err = rel_rows(run(x, M.FFT_INVERSE, adjoint=True), O.fft(x, "adjoint_inverse", c=64))
+    err = err_rows(run(x, M.FFT_INVERSE, adjoint=True), O.fft(x, "adjoint_inverse", c=64))
     assert err.max() <= 1e-12
-    err = rel_rows(run(x, inplace=True), O.fft(x, "forward", c=64))
+    err = err_rows(run(x, inplace=True), O.fft(x, "forward", c=64))
     assert err.max() <= 1e-12
 
 
@@ -74,7 +72,7 @@ def test_df64_full_size_sampled():
     picks = [0, 33, 63]
     y = run(x, rows=picks)
     ref = O.fft(x[picks], "forward", c=1024, threads=3)
-    assert rel_rows(y, ref).max() <= 1e-12
+    assert err_rows(y, ref).max() <= 1e-12
 
 
 def test_df64_rejects_small_and_c64():
@@ -84,3 +82,36 @@ def test_df64_rejects_small_and_c64():
     with pytest.raises(M.MoaFFTError) as e:
         M.fft_plan_ex(1024, 1, M.FFT_C64, M.FFT_FORWARD, M.FFT_FORM_DF64)
     assert e.value.status == M.FFT_ERR_UNSUPPORTED
+
+
+def test_df64_dynamic_range_input():
+    """Amplitudes log-uniform over 1e-4..1e4 (the precision-form input):
+    the double-float form keeps the FP64 tolerance."""
+    n = 1 << 16
+    x = W.dynamic_range_complex(n, 4, seed=0)
+    assert err_rows(run(x), O.fft(x, "forward", c=1024, threads=4)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e30])
+def test_df64_inside_the_fp32_exponent_range(scale):
+    """Inputs scaled far from 1 but inside the range the header states
+    (every value and partial sum between about 2e-31 and 3.4e38): the FP64
+    tolerance holds."""
+    n = 1024
+    x = W.uniform_complex(n, 3, seed=31) * scale
+    for direction, op in ((M.FFT_FORWARD, "forward"), (M.FFT_INVERSE, "inverse")):
+        assert err_rows(run(x, direction), O.fft(x, op, c=64)).max() <= 1e-12
+
+
+def test_df64_outside_the_fp32_exponent_range():
+    """What the header documents beyond that range, checked as stated: near
+    1e-35 the low float falls into FP32's subnormals and the result is only
+    about single-precision accurate (still within the FP32 form's tolerance);
+    a result beyond 3.4e38 is infinite (n times a constant 1e36)."""
+    n = 1024
+    x = W.uniform_complex(n, 2, seed=32) * 1e-35
+    err = err_rows(run(x), O.fft(x, "forward", c=64))
+    assert err.max() <= 1e-6 * 10
+    big = np.full((1, n), 1e36, dtype=np.complex128)
+    y = run(big)
+    assert np.isinf(y[0, 0].real)

@@ -8,6 +8,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -22,9 +23,6 @@ def gpu():
     yield
 
 
-def rel_rows(a, b):
-    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
-
 
 def test_pageable_complex128_every_row():
     n, batch = 1 << 12, 37
@@ -36,7 +34,7 @@ def test_pageable_complex128_every_row():
         torch.cuda.synchronize()
     finally:
         M.fft_destroy(p)
-    assert rel_rows(y, O.fft(x, "forward", c=64, threads=4)).max() <= 1e-12
+    assert err_rows(y, O.fft(x, "forward", c=64, threads=4)).max() <= 1e-12
 
 
 def test_pinned_complex64_several_slots():
@@ -55,7 +53,7 @@ def test_pinned_complex64_several_slots():
     y = yout.numpy().astype(np.complex128)
     xr = x.astype(np.complex128)
     rows = [0, 1, 127, 128, 255, 256, 299]  # both sides of every slice boundary
-    assert rel_rows(y[rows], O.fft(xr[rows], "forward", c=256, threads=4)).max() <= 1.6e-5
+    assert err_rows(y[rows], O.fft(xr[rows], "forward", c=256, threads=4)).max() <= 1.6e-5
     ex = np.sum(np.abs(xr) ** 2, axis=-1)
     assert np.max(np.abs(np.sum(np.abs(y) ** 2, axis=-1) - n * ex) / (n * ex)) <= 1e-5
 
@@ -70,7 +68,7 @@ def test_in_place_inverse():
         torch.cuda.synchronize()
     finally:
         M.fft_destroy(p)
-    assert rel_rows(buf, O.fft(x, "inverse", c=64)).max() <= 1e-12
+    assert err_rows(buf, O.fft(x, "inverse", c=64)).max() <= 1e-12
 
 
 def test_rejects_uneven_plans_and_device_pointers():
@@ -111,5 +109,5 @@ def test_chained_calls_are_stream_ordered():
     finally:
         M.fft_destroy(pf)
         M.fft_destroy(pi)
-    err = rel_rows(back.numpy().astype(np.complex128), x.astype(np.complex128))
+    err = err_rows(back.numpy().astype(np.complex128), x.astype(np.complex128))
     assert err.max() <= 1e-6 * 16

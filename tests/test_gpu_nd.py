@@ -13,6 +13,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_arrays, err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -30,11 +31,6 @@ def gpu():
 def tol(dt, n):
     return 1e-12 if dt == M.FFT_C128 else 1e-6 * max(1, int(math.log2(n)))
 
-
-def rel_arrays(a, b):
-    a = a.reshape(a.shape[0], -1)
-    b = b.reshape(b.shape[0], -1)
-    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
 
 
 def seeded(batch, dims, seed):
@@ -77,7 +73,7 @@ def test_nd_forward_inverse(dt, dims):
     for op, direction, adjoint in ops:
         y = run_nd(x, dims, dt, direction, adjoint)
         ref = O.fftn(xr, ndim=len(dims), op=op, c=64, threads=4)
-        err = rel_arrays(y, ref)
+        err = err_arrays(y, ref)
         assert err.max() <= tol(dt, n), (dims, op, err.max())
 
 
@@ -86,9 +82,9 @@ def test_nd_in_place_and_roundtrip(dt):
     dims = (32, 8, 64)
     x = seeded(2, dims, 77)
     y = run_nd(x, dims, dt, inplace=True)
-    assert rel_arrays(y, O.fftn(rounded(x, dt), ndim=3, c=64)).max() <= tol(dt, 32 * 8 * 64)
+    assert err_arrays(y, O.fftn(rounded(x, dt), ndim=3, c=64)).max() <= tol(dt, 32 * 8 * 64)
     back = run_nd(y, dims, dt, M.FFT_INVERSE, inplace=True)
-    assert rel_arrays(back, rounded(x, dt)).max() <= 2 * tol(dt, 32 * 8 * 64)
+    assert err_arrays(back, rounded(x, dt)).max() <= 2 * tol(dt, 32 * 8 * 64)
 
 
 def test_nd_closed_forms_c128():
@@ -124,8 +120,8 @@ def test_nd_plan_structure_and_wrappers():
     x = torch.from_numpy(seeded(3, (16, 32), 5)).cuda()
     X = M.fftn(x, ndim=2)
     ref = O.fftn(seeded(3, (16, 32), 5), ndim=2)
-    assert rel_arrays(X.cpu().numpy(), ref).max() <= 1e-12
-    assert rel_arrays(M.ifftn(X, ndim=2).cpu().numpy(), seeded(3, (16, 32), 5)).max() <= 1e-12
+    assert err_arrays(X.cpu().numpy(), ref).max() <= 1e-12
+    assert err_arrays(M.ifftn(X, ndim=2).cpu().numpy(), seeded(3, (16, 32), 5)).max() <= 1e-12
 
 
 def test_nd_long_axis_takes_two_passes():
@@ -150,7 +146,7 @@ def test_nd_full_size_c64_4096_squared():
     x = seeded(1, dims, 9)
     y = run_nd(x, dims, M.FFT_C64)
     ref = O.fftn(rounded(x, M.FFT_C64), ndim=2, c=4096, threads=4)
-    assert rel_arrays(y, ref).max() <= tol(M.FFT_C64, 1 << 24)
+    assert err_arrays(y, ref).max() <= tol(M.FFT_C64, 1 << 24)
 
 
 @pytest.mark.parametrize("inverse", [False, True])
@@ -178,4 +174,4 @@ def test_nd_autograd_gradient_vs_oracle_adjoint():
     Xn = O.fftn(xn, ndim=2)
     expect = O.fftn(2 * (Xn * Hn - yn) * np.conj(Hn), ndim=2, op="adjoint_forward")
     got = x.grad.cpu().numpy()
-    assert np.linalg.norm(got - expect) / np.linalg.norm(expect) <= 1e-12
+    assert err_arrays(got[None], expect[None]).max() <= 1e-12

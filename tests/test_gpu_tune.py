@@ -9,6 +9,7 @@ import pytest
 import oracle as O
 import paper_0803_2386_gb300 as M
 import workloads as W
+from parity_check import err_one, err_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +37,7 @@ def test_auto_schedule_is_cached_and_reused(tmp_path, monkeypatch):
     torch.cuda.synchronize()
     M.fft_destroy(p)
     ref = O.fft(x.astype(np.complex64).astype(np.complex128), "forward", c=256)
-    err = np.linalg.norm(out.cpu().numpy() - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    err = err_rows(out.cpu().numpy(), ref)
     assert err.max() <= 1e-6 * 14
     lines = [json.loads(l) for l in cache.read_text().splitlines()]
     assert len(lines) == 1 and lines[0]["schedule"] in M.fft_tune_candidates(n, M.FFT_C64)
