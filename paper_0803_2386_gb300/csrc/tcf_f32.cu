@@ -31,7 +31,7 @@ static cudaError_t launch_tcf_one(const PassArgs &a, cudaStream_t s)
         // the digit-split pass weights come with the tile through the TMA
         // engine when their tables allow a tensor map
         tma_w = !no_tma_w && a.tw_mode == 3 && a.col_shift == 0 &&
-                table_tensor_map(a.tw_pass, a.B, G::U, W, G::U, &maps.tw1) &&
+                (G::U_STAGED == 0 || table_tensor_map(a.tw_pass, a.B, G::U, W, G::U, &maps.tw1)) &&
                 table_tensor_map(a.tw_hi, a.B, 16, W, 16, &maps.tw2);
     }
     // shared memory (and so the CTAs per SM) with and without the weights

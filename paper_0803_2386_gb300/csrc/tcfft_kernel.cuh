@@ -55,6 +55,10 @@
 
 namespace moafft {
 
+// suspend-time hint of the kernel's mbarrier waits: with at most 2^20 /
+// 2^22 polls a wait gives up after about one / four seconds
+constexpr uint32_t kTcfSleepNs = 1000;
+
 template <int LOGD> struct TcfGeo {
     static constexpr int D = 1 << LOGD;
     static constexpr int LOGR = 2 * LOGD;
@@ -69,6 +73,9 @@ template <int LOGD> struct TcfGeo {
     // reads at once in different banks
     static constexpr int PITCH = R + (D == 16 ? 2 : 4);
     static constexpr int U = R / 16;          // rows of the first pass-weight table (digit split of k)
+    // staged rows of the first pass-weight table: D = 16 reads its one
+    // factor per thread from memory (the stage then fits four CTAs per SM)
+    static constexpr int U_STAGED = U > D ? U : 0;
     static constexpr int BR = R < 256 ? R : 256;  // rows per tensor-map box
     static constexpr uint32_t TMEM_COLS = K < 32 ? 32 : K;
 };
@@ -81,7 +88,7 @@ __host__ __device__ constexpr size_t tcf_stage_elems(bool with_weights)
 {
     using G = TcfGeo<LOGD>;
     return LAST ? (size_t)G::W * G::PITCH
-                : (size_t)G::R * G::W + (with_weights ? (size_t)(G::U + 16) * G::W : 0);
+                : (size_t)G::R * G::W + (with_weights ? (size_t)(G::U_STAGED + 16) * G::W : 0);
 }
 
 template <int LOGD, bool LAST>
@@ -100,10 +107,11 @@ __host__ __device__ __forceinline__ uint32_t tcf_off(int row, int k)
     return (uint32_t)((row >> 3) * TcfGeo<LOGD>::SBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// One complex value as two (re, im) pairs of 16-bit numbers, hi + lo: hi
-// keeps the leading 11 (FP16) or 8 (BF16) significant bits of each part by
-// truncation, so it converts exactly; lo = x - hi (exact in FP32) rounded
-// once.  One packed conversion per pair.
+// One complex value as two (re, im) pairs of 16-bit numbers, hi + lo, one
+// packed conversion per pair.  FP16: hi keeps the leading 11 significant
+// bits of each part by truncation, so it converts exactly; lo = x - hi
+// (exact in FP32) rounded once.  BF16: hi is x rounded to bf16 (its float
+// value is the bf16 bits shifted up), lo = x - hi rounded once.
 template <bool BF16>
 __device__ __forceinline__ void tcf_split(float re, float im, uint32_t &hi, uint32_t &lo)
 {
@@ -111,10 +119,13 @@ __device__ __forceinline__ void tcf_split(float re, float im, uint32_t &hi, uint
     const float hr = __uint_as_float(__float_as_uint(re) & mask);
     const float hm = __uint_as_float(__float_as_uint(im) & mask);
     if constexpr (BF16) {
-        // the high halves of the two floats are the bf16 values themselves
-        hi = __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x7632);
-        const __nv_bfloat162 l2 = __floats2bfloat162_rn(re - hr, im - hm);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(re, im);
+        hi = *reinterpret_cast<const uint32_t *>(&h2);
+        const float hr2 = __uint_as_float(hi << 16), hm2 = __uint_as_float(hi & 0xFFFF0000u);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(re - hr2, im - hm2);
         lo = *reinterpret_cast<const uint32_t *>(&l2);
+        (void)hr;
+        (void)hm;
     } else {
         const __half2 h2 = __floats2half2_rn(hr, hm);
         const __half2 l2 = __floats2half2_rn(re - hr, im - hm);
@@ -188,14 +199,14 @@ __device__ __forceinline__ void tcf_issue(const PassArgs &p, const TcfMaps *maps
         const int64_t a = rem / colgroups;
         const int64_t b0 = (rem - a * colgroups) * W;
         if (lane == 0) {
-            const uint32_t wbytes = tma_w ? (uint32_t)((G::U + 16) * W * sizeof(float2)) : 0u;
+            const uint32_t wbytes = tma_w ? (uint32_t)((G::U_STAGED + 16) * W * sizeof(float2)) : 0u;
             tc::mbar_arrive_expect_tx(mbar, (uint32_t)(R * W * sizeof(float2)) + wbytes);
             const int64_t y0 = (tr * p.A + a) * R;
             for (int k = 0; k < R / G::BR; k++)
                 tc::tensor_g2s_2d(stage + (size_t)k * G::BR * W, &maps->sig, (int)b0, (int)(y0 + k * G::BR), mbar);
             if (tma_w) {
-                tc::tensor_g2s_2d(stage + (size_t)R * W, &maps->tw1, (int)b0, 0, mbar);
-                tc::tensor_g2s_2d(stage + (size_t)(R + G::U) * W, &maps->tw2, (int)b0, 0, mbar);
+                if (G::U_STAGED) tc::tensor_g2s_2d(stage + (size_t)R * W, &maps->tw1, (int)b0, 0, mbar);
+                tc::tensor_g2s_2d(stage + (size_t)(R + G::U_STAGED) * W, &maps->tw2, (int)b0, 0, mbar);
             }
         }
     } else {
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
     for (int it = 0; t < total; t += GS, it++) {
         const int buf = it & 1;
         const uint32_t parity = (uint32_t)((it >> 1) & 1);
-        if (!tc::mbar_wait(&mbar_st[buf], parity, kBulkWaitPolls)) failed = true;
+        if (!tc::mbar_wait_sleep(&mbar_st[buf], parity, kBulkWaitPolls, kTcfSleepNs)) failed = true;
         const float2 *st = stage + buf * SE;
         float2 v[D];
 #pragma unroll
@@ -358,9 +369,13 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
         // this tile's first pass-weight factors, staged with it (column passes)
         float2 wt1a = make_float2(1.f, 0.f), wt1b = make_float2(1.f, 0.f);
         if (tmaw) {
-            const float2 *t1s = st + (size_t)R * W;
-            wt1a = t1s[k1 * W + w];                             // r = k1
-            if constexpr (U > D) wt1b = t1s[(k1 + D) * W + w];  // r = k1 + D (D = 32)
+            if constexpr (G::U_STAGED) {
+                const float2 *t1s = st + (size_t)R * W;
+                wt1a = t1s[k1 * W + w];        // r = k1
+                wt1b = t1s[(k1 + D) * W + w];  // r = k1 + D
+            } else {
+                wt1a = __ldg(reinterpret_cast<const float2 *>(p.tw_pass) + (int64_t)k1 * p.B + bcol);  // r = k1
+            }
         }
         // ---- digit-1 operand: per-vector power-of-two scale (FP16)
         int e1 = 0;
@@ -390,7 +405,7 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
         float2 tw[D];
 #pragma unroll
         for (int k = 0; k < D; k++) tw[k] = __ldg(twt + ((mq * k) & (R - 1)));
-        if (!tc::mbar_wait(&mbar_mma, mma_phase, kTcWaitPolls)) failed = true;
+        if (!tc::mbar_wait_sleep(&mbar_mma, mma_phase, kTcWaitPolls, kTcfSleepNs)) failed = true;
         mma_phase ^= 1u;
         tc::fence_after_sync();
         float d[K];
@@ -430,11 +445,11 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
         // the pass weights' second factors, w_M^(b U j), while the products run
         float2 wt2[16];
         if (tmaw) {
-            const float2 *t2s = st + (size_t)(R + U) * W;
+            const float2 *t2s = st + (size_t)(R + G::U_STAGED) * W;
 #pragma unroll
             for (int j = 0; j < 16; j++) wt2[j] = t2s[j * W + w];
         }
-        if (!tc::mbar_wait(&mbar_mma, mma_phase, kTcWaitPolls)) failed = true;
+        if (!tc::mbar_wait_sleep(&mbar_mma, mma_phase, kTcWaitPolls, kTcfSleepNs)) failed = true;
         mma_phase ^= 1u;
         tc::fence_after_sync();
         tcf_read<LOGD>(tmem, d);

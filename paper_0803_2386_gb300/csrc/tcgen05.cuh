@@ -113,6 +113,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
     return false;
 }
 
+// As mbar_wait, with a suspend-time hint: a thread whose phase has not
+// completed sleeps for up to hint_ns before the next poll instead of
+// spinning (fewer issue slots taken from the other warps); gives up after
+// max_iter polls.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *mbar, uint32_t parity, uint32_t max_iter, uint32_t hint_ns)
+{
+    const uint32_t a = smem_u32(mbar);
+    for (uint32_t it = 0; it < max_iter; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // ---- tensor memory -> registers: 32 lanes x 32 columns of 32 bits ------
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 {
