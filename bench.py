@@ -949,6 +949,33 @@ def extra_configs(M, torch, dev, stream):
         _emit(row)
         del x, y
 
+    # tensor-core DFT digits of 16 and 32 points at n = 2^24 (the paper's
+    # radix sweep, Table 4, is at 2^24): passes of 2^8 = 16 x 16 (both digits
+    # as tcgen05 products) against passes of 2^10 = 32 x 32 for 20 of the 24
+    # stages; errors against the complex128 plan on two transforms
+    n, batch = 1 << 24, 8
+    gen = torch.Generator(device=dev).manual_seed(25)
+    x = torch.randn(batch, n, dtype=torch.complex64, device=dev, generator=gen)
+    y = torch.empty_like(x)
+    with M.Plan(n, 2, M.FFT_C128, M.FFT_FORWARD) as pr:
+        xr = x[:2].to(torch.complex128)
+        yr = torch.empty_like(xr)
+        pr.exec(xr, yr, stream)
+    row = {"config": f"tensor-core radix sweep, c64 n=2^24 batch {batch} forward"}
+    for form, fname in ((M.FFT_FORM_TC_FP16, "fp16"), (M.FFT_FORM_TC_BF16, "bf16")):
+        for sched, key in (("8,8,8", "radix16"), ("10,10,4", "radix32")):
+            p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form, sched)
+            ms = _time(torch, stream, lambda: p.exec(x, y, stream), 3)
+            M.fft_plan_check(p.handle)
+            row[f"{fname}_{key}_ms"] = round(ms, 3)
+            row[f"{fname}_{key}_rel_err"] = rel(y[:2], yr)
+            p.close()
+    p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD)
+    row["fp32_default_ms"] = round(_time(torch, stream, lambda: p.exec(x, y, stream), 3), 3)
+    p.close()
+    _emit(row)
+    del x, y, xr, yr
+
     # density-matrix gating by hyper-cube transpose: 14 qubits (2^28 elements,
     # larger than L2), in place; algorithmic bytes = one read + one write;
     # flops = the two 2^q x 2^q complex products per block

@@ -1622,9 +1622,32 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
         for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(p->s_comp[k], p->ev_start, 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (stream order)");
     }
-    for (int64_t b0 = 0, i = 0; b0 < p->batch; b0 += p->stage_tr, i++) {
+    // Slices of stage_tr transforms, ramped at both ends (from an eighth of a
+    // slot, doubling, up; the mirror image down): the first slice's copy in
+    // and the last slice's copy out overlap no transform, so short ones there
+    // shorten the pipeline's fill and drain, while full slots in between keep
+    // the launches few.
+    std::vector<int64_t> slices;
+    {
+        int64_t rem = p->batch, up = std::max<int64_t>(1, p->stage_tr / 8);
+        std::vector<int64_t> tail;
+        while (rem > 0 && up < p->stage_tr && rem > 2 * up) {  // ramp up, and the mirrored ramp down
+            slices.push_back(up);
+            tail.push_back(up);
+            rem -= 2 * up;
+            up *= 2;
+        }
+        while (rem > 0) {
+            const int64_t c = std::min(p->stage_tr, rem);
+            slices.push_back(c);
+            rem -= c;
+        }
+        slices.insert(slices.end(), tail.rbegin(), tail.rend());
+    }
+    int64_t b0 = 0;
+    for (size_t i = 0; i < slices.size(); b0 += slices[i], i++) {
         int k = (int)(i & 1);
-        int64_t cnt = std::min(p->stage_tr, p->batch - b0);
+        int64_t cnt = slices[i];
         size_t off = (size_t)b0 * p->n * eb, bytes = (size_t)cnt * p->n * eb;
         cudaError_t e = cudaSuccess;
         if (used[k]) e = cudaStreamWaitEvent(p->s_h2d, p->ev_comp[k], 0);

@@ -72,7 +72,31 @@ template <> struct cvec<dfloat> { using type = dcplx; };
 // float.  Where it would not be, lo keeps the bits an FP32 subnormal holds
 // (resolution 2^-149), and a double below FP32's normal range becomes a
 // subnormal hi (truncated) with lo = 0: precision fades out gradually down
-// to 2^-149, below which a value becomes 0.
+// to 2^-149, below which a value becomes 0.  Doubles beyond FP32's range
+// become infinite.  Integer operations only.  The rare cases sit in
+// functions of their own, so the code inlined at every load stays short.
+static __device__ __noinline__ dfloat df_from_double_rare(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const int ef = e - 1023 + 127;
+    if (ef >= 255) return dfloat(__uint_as_float(sgn | 0x7f800000u), 0.f);  // overflow: infinity
+    if (ef <= 0) {
+        // |x| < 2^-126: hi = (2^52 + m) 2^(e - 1075) as f 2^-149, f = that >> (926 - e)
+        const int sh = 926 - e;  // >= 30
+        const uint32_t f = (e == 0 || sh >= 64) ? 0u : (uint32_t)(((1ull << 52) | m) >> sh);
+        return dfloat(__uint_as_float(sgn | f), __uint_as_float(sgn));
+    }
+    // lo = r 2^(e - 1075) below 2^-126: the subnormal f 2^-149, f = r 2^(e - 926) (< 2^23)
+    const float hi = __uint_as_float(sgn | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
+    const uint32_t r = (uint32_t)(m & 0x1FFFFFFFull);
+    const int up = e - 926;
+    const uint32_t f = up >= 0 ? (r << up) : (-up >= 32 ? 0u : (r >> -up));
+    return dfloat(hi, __uint_as_float(sgn | (f & 0x7FFFFFu)));
+}
+
 __device__ __forceinline__ dfloat df_from_double(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -80,51 +104,24 @@ __device__ __forceinline__ dfloat df_from_double(double x)
     const int e = (int)((b >> 52) & 0x7ff);
     const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
     const int ef = e - 1023 + 127;
-    if (ef <= 0) {
-        // |x| < 2^-126: hi = (2^52 + m) 2^(e - 1075) as f 2^-149, f = that >> (926 - e)
-        const int sh = 926 - e;  // >= 30
-        const uint32_t f = (e == 0 || sh >= 64) ? 0u : (uint32_t)(((1ull << 52) | m) >> sh);
-        return dfloat(__uint_as_float(sgn | f), __uint_as_float(sgn));
-    }
-    if (ef >= 255) return dfloat(__uint_as_float(sgn | 0x7f800000u), 0.f);  // overflow: infinity
-    const float hi = __uint_as_float(sgn | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
     const uint32_t r = (uint32_t)(m & 0x1FFFFFFFull);  // the 29 bits below hi: lo = r 2^(e - 1075)
+    const int p = 31 - __clz(r);                       // leading one of r (-1 when r = 0)
+    const int el = p + e - 1075 + 127;                 // float exponent of lo
+    if (ef <= 0 || ef >= 255 || (r != 0 && el <= 0)) return df_from_double_rare(x);
+    const float hi = __uint_as_float(sgn | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
     if (r == 0) return dfloat(hi, 0.f);
-    const int p = 31 - __clz(r);            // leading one of r, 0..28
-    const int el = p + e - 1075 + 127;      // float exponent of lo
-    if (el <= 0) {
-        // lo below 2^-126: the subnormal f 2^-149 with f = r 2^(e - 926) (< 2^23 here)
-        const int up = e - 926;
-        const uint32_t f = up >= 0 ? (r << up) : (-up >= 32 ? 0u : (r >> -up));
-        return dfloat(hi, __uint_as_float(sgn | (f & 0x7FFFFFu)));
-    }
     const uint32_t frac = p <= 23 ? (r << (23 - p)) & 0x7FFFFFu : (r >> (p - 23)) & 0x7FFFFFu;
     return dfloat(hi, __uint_as_float(sgn | ((uint32_t)el << 23) | frac));
 }
 
 // hi + lo rounded toward zero to a double (|lo| < ulp(hi) assumed, which
-// every operation above guarantees); subnormal floats count with their
-// value (hi subnormal: the double holds it exactly, lo is then below
-// 2^-149 and 0).
-__device__ __forceinline__ double df_to_double(dfloat v)
+// every operation above guarantees); subnormal floats count with their value
+// (hi subnormal: the double holds it exactly, lo is then below 2^-149 and
+// 0).  The significand sum of hi and a (normal or subnormal) lo.
+__device__ __forceinline__ double df_to_double_sum(uint32_t bh, uint32_t bl, int eh, int el)
 {
-    const uint32_t bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
-    const int eh = (int)((bh >> 23) & 0xff);
-    if (eh == 0) {
-        // subnormal (or zero) hi: f 2^-149 converts exactly (integer bits)
-        const uint32_t f = bh & 0x7FFFFFu;
-        unsigned long long bits = (unsigned long long)(bh >> 31) << 63;
-        if (f) {
-            const int p = 31 - __clz(f);  // f = 1.xxx 2^p
-            bits |= ((unsigned long long)(p - 149 + 1023) << 52) |
-                    (((unsigned long long)f << (52 - p)) & 0xFFFFFFFFFFFFFull);
-        }
-        return __longlong_as_double((long long)bits);
-    }
-    if (eh == 0xff) return __longlong_as_double((long long)(((unsigned long long)(bh >> 31) << 63) | 0x7FF0000000000000ull));
     long long m = (long long)((unsigned long long)((bh & 0x7FFFFFu) | 0x800000u) << 29);  // 53-bit significand
-    const int el = (int)((bl >> 23) & 0xff);
-    if (el != 0xff && (bl & 0x7FFFFFFFu) != 0) {
+    if ((bl & 0x7FFFFFFFu) != 0) {
         // lo = ml 2^(el - 150): normal (implicit bit) or subnormal (el taken as 1)
         const unsigned long long ml =
             el ? (unsigned long long)((bl & 0x7FFFFFu) | 0x800000u) : (unsigned long long)(bl & 0x7FFFFFu);
@@ -145,6 +142,35 @@ __device__ __forceinline__ double df_to_double(dfloat v)
     const unsigned long long bits = ((unsigned long long)(bh >> 31) << 63) | ((unsigned long long)e << 52) |
                                     ((unsigned long long)m & 0xFFFFFFFFFFFFFull);
     return __longlong_as_double((long long)bits);
+}
+
+static __device__ __noinline__ double df_to_double_rare(uint32_t bh, uint32_t bl)
+{
+    const int eh = (int)((bh >> 23) & 0xff);
+    if (eh == 0) {
+        // subnormal (or zero) hi: f 2^-149 converts exactly
+        const uint32_t f = bh & 0x7FFFFFu;
+        unsigned long long bits = (unsigned long long)(bh >> 31) << 63;
+        if (f) {
+            const int p = 31 - __clz(f);  // f = 1.xxx 2^p
+            bits |= ((unsigned long long)(p - 149 + 1023) << 52) |
+                    (((unsigned long long)f << (52 - p)) & 0xFFFFFFFFFFFFFull);
+        }
+        return __longlong_as_double((long long)bits);
+    }
+    if (eh == 0xff) return __longlong_as_double((long long)(((unsigned long long)(bh >> 31) << 63) | 0x7FF0000000000000ull));
+    // subnormal lo (or infinite lo, ignored)
+    const int el = (int)((bl >> 23) & 0xff);
+    return df_to_double_sum(bh, el == 0xff ? 0u : bl, eh, el == 0xff ? 0 : el);
+}
+
+__device__ __forceinline__ double df_to_double(dfloat v)
+{
+    const uint32_t bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
+    const int eh = (int)((bh >> 23) & 0xff);
+    const int el = (int)((bl >> 23) & 0xff);
+    if (eh == 0 || eh == 0xff || el == 0xff || (el == 0 && (bl & 0x7FFFFFFFu) != 0)) return df_to_double_rare(bh, bl);
+    return df_to_double_sum(bh, bl, eh, el);
 }
 
 __device__ __forceinline__ dcplx dc_from(double2 a) { return dcplx{df_from_double(a.x), df_from_double(a.y)}; }

@@ -52,7 +52,9 @@ def test_pinned_complex64_several_slots():
         M.fft_destroy(p)
     y = yout.numpy().astype(np.complex128)
     xr = x.astype(np.complex128)
-    rows = [0, 1, 127, 128, 255, 256, 299]  # both sides of every slice boundary
+    # both sides of every multiple of 16 rows (the slices, ramped at both
+    # ends, start at multiples of 16 here)
+    rows = sorted({0, batch - 1} | {r for b in range(16, batch, 16) for r in (b - 1, b)})
     assert err_rows(y[rows], O.fft(xr[rows], "forward", c=256, threads=4)).max() <= 1.6e-5
     ex = np.sum(np.abs(xr) ** 2, axis=-1)
     assert np.max(np.abs(np.sum(np.abs(y) ** 2, axis=-1) - n * ex) / (n * ex)) <= 1e-5
@@ -111,3 +113,20 @@ def test_chained_calls_are_stream_ordered():
         M.fft_destroy(pi)
     err = err_rows(back.numpy().astype(np.complex128), x.astype(np.complex128))
     assert err.max() <= 1e-6 * 16
+
+
+def test_pinned_complex128_ramped_slices():
+    """complex128 n = 2^20 x 9 through 64 MiB slots of 4 transforms: the
+    slices ramp up and down (1, 2, 3, 2, 1 transforms), every transform
+    against the oracle."""
+    n, batch = 1 << 20, 9
+    x = W.uniform_complex(n, batch, seed=72)
+    xin = torch.from_numpy(x).pin_memory()
+    yout = torch.empty_like(xin).pin_memory()
+    p = M.fft_plan(n, batch, M.FFT_C128, M.FFT_FORWARD)
+    try:
+        M.fft_exec_host(p, xin, yout)
+        torch.cuda.synchronize()
+    finally:
+        M.fft_destroy(p)
+    assert err_rows(yout.numpy(), O.fft(x, "forward", c=1024, threads=4)).max() <= 1e-12

@@ -94,6 +94,7 @@ def describe_schedule(p):
     (20, None, 2),                        # 10, 10
     (16, "10,6", 2), (16, "6,10", 2),     # a 32 x 32 pass beside a per-tile pass
     (24, "8,8,8", 1),                     # three passes: the middle one reads the last pass's digit order
+    (24, "10,10,4", 1),                   # 32 x 32 passes first and in the middle (the radix sweep's schedule)
 ])
 def test_tc_two_digit_passes(form, t, schedule, batch):
     """Passes of 2^8 = 16 x 16 and 2^10 = 32 x 32 points, whose two DFT
