@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other forms (df64, precision, uneven, adjoint)")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "c128", "df64", "dm", "nd2d"],
+    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "tc32", "c128", "df64", "dm", "nd2d"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -1037,6 +1037,7 @@ def run_case(args):
         print("ok")
         return 0
     form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
+            "tc32": M.FFT_FORM_TC_FP16,
             "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN,
             "c64_rows": M.FFT_FORM_PLAIN, "c1": M.FFT_FORM_PLAIN}[args.case]
     if args.case == "c1":  # one complex128 transform of 2^10 points (latency)
@@ -1049,6 +1050,11 @@ def run_case(args):
         x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
         y = torch.empty_like(x)
         p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form)
+    elif args.case == "tc32":  # complex64 n = 2^20 x 32 (256 MiB), two passes of 32 x 32 tensor-core digits
+        n, batch = 1 << 20, 32
+        x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form, "10,10;chunk=32")
     elif args.case in ("c128", "df64"):
         n, batch = 1 << 20, 16
         x = torch.randn(batch, n, dtype=torch.complex128, device="cuda")

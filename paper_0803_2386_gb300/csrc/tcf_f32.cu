@@ -14,8 +14,8 @@ template <int DIR, int LOGD, bool LAST, bool BF16>
 static cudaError_t launch_tcf_one(const PassArgs &a, cudaStream_t s)
 {
     using G = TcfGeo<LOGD>;
-    // MOAFFT_TCF_NO_TMA_W: the pass weights by global loads instead of with
-    // the tile (comparison; the stage then also holds fewer bytes)
+    // MOAFFT_TCF_NO_TMA_W: every pass weight by its own global loads
+    // (comparison; the stage then also holds fewer bytes)
     static const bool no_tma_w = getenv("MOAFFT_TCF_NO_TMA_W") != nullptr;
     constexpr int W = G::W;
     int64_t ctas;
@@ -28,11 +28,11 @@ static cudaError_t launch_tcf_one(const PassArgs &a, cudaStream_t s)
     int tma_w = 0;
     if (!LAST) {
         if (!column_tensor_map(a, W, &maps.sig)) return cudaErrorNotSupported;
-        // the digit-split pass weights come with the tile through the TMA
-        // engine when their tables allow a tensor map
+        // the digit-split pass weights: the second table's columns come with
+        // the tile through the TMA engine (16 x 16) when it allows a tensor
+        // map, or from two loads and their powers (32 x 32)
         tma_w = !no_tma_w && a.tw_mode == 3 && a.col_shift == 0 &&
-                (G::U_STAGED == 0 || table_tensor_map(a.tw_pass, a.B, G::U, W, G::U, &maps.tw1)) &&
-                table_tensor_map(a.tw_hi, a.B, 16, W, 16, &maps.tw2);
+                (!G::STAGE_T2 || table_tensor_map(a.tw_hi, a.B, 16, W, 16, &maps.tw2));
     }
     // shared memory (and so the CTAs per SM) with and without the weights
     static DeviceOnce setup[2];

@@ -73,22 +73,23 @@ template <int LOGD> struct TcfGeo {
     // reads at once in different banks
     static constexpr int PITCH = R + (D == 16 ? 2 : 4);
     static constexpr int U = R / 16;          // rows of the first pass-weight table (digit split of k)
-    // staged rows of the first pass-weight table: D = 16 reads its one
-    // factor per thread from memory (the stage then fits four CTAs per SM)
-    static constexpr int U_STAGED = U > D ? U : 0;
+    // D = 16 stages the tile's columns of the second pass-weight table with
+    // its points; D = 32 (whose stage must stay small enough for two CTAs
+    // per SM) forms them as powers of one entry
+    static constexpr bool STAGE_T2 = D == 16;
     static constexpr int BR = R < 256 ? R : 256;  // rows per tensor-map box
     static constexpr uint32_t TMEM_COLS = K < 32 ? 32 : K;
 };
 
-// one stage: the tile's points, and (column passes whose pass weights come
-// with the tile) the tile's columns of the two pass-weight tables, U + 16
-// rows of W entries
+// one stage: the tile's points, and (16 x 16 column passes whose pass
+// weights come with the tile) the tile's columns of the second pass-weight
+// table, 16 rows of W entries
 template <int LOGD, bool LAST>
 __host__ __device__ constexpr size_t tcf_stage_elems(bool with_weights)
 {
     using G = TcfGeo<LOGD>;
     return LAST ? (size_t)G::W * G::PITCH
-                : (size_t)G::R * G::W + (with_weights ? (size_t)(G::U_STAGED + 16) * G::W : 0);
+                : (size_t)G::R * G::W + (with_weights && G::STAGE_T2 ? (size_t)16 * G::W : 0);
 }
 
 template <int LOGD, bool LAST>
@@ -177,10 +178,10 @@ __device__ __forceinline__ int64_t tcf_unrev(const PassArgs &p, int64_t vrow)
     return a;
 }
 
-// Tensor maps of a launch: the signal (column passes) and the two
-// pass-weight tables of the digit split (column passes with tw_mode 3).
+// Tensor maps of a launch: the signal (column passes) and the second
+// pass-weight table of the digit split (16 x 16 column passes, tw_mode 3).
 struct TcfMaps {
-    CUtensorMap sig, tw1, tw2;
+    CUtensorMap sig, tw2;
 };
 
 // warp 0: start the copies of tile `cta` into `stage`
@@ -199,15 +200,12 @@ __device__ __forceinline__ void tcf_issue(const PassArgs &p, const TcfMaps *maps
         const int64_t a = rem / colgroups;
         const int64_t b0 = (rem - a * colgroups) * W;
         if (lane == 0) {
-            const uint32_t wbytes = tma_w ? (uint32_t)((G::U_STAGED + 16) * W * sizeof(float2)) : 0u;
+            const uint32_t wbytes = tma_w && G::STAGE_T2 ? (uint32_t)(16 * W * sizeof(float2)) : 0u;
             tc::mbar_arrive_expect_tx(mbar, (uint32_t)(R * W * sizeof(float2)) + wbytes);
             const int64_t y0 = (tr * p.A + a) * R;
             for (int k = 0; k < R / G::BR; k++)
                 tc::tensor_g2s_2d(stage + (size_t)k * G::BR * W, &maps->sig, (int)b0, (int)(y0 + k * G::BR), mbar);
-            if (tma_w) {
-                if (G::U_STAGED) tc::tensor_g2s_2d(stage + (size_t)R * W, &maps->tw1, (int)b0, 0, mbar);
-                tc::tensor_g2s_2d(stage + (size_t)(R + G::U_STAGED) * W, &maps->tw2, (int)b0, 0, mbar);
-            }
+            if (tma_w && G::STAGE_T2) tc::tensor_g2s_2d(stage + (size_t)R * W, &maps->tw2, (int)b0, 0, mbar);
         }
     } else {
         const float2 *in = reinterpret_cast<const float2 *>(p.in);
@@ -366,15 +364,16 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
             obase = tr * p.n;
             ostride = 1;
         }
-        // this tile's first pass-weight factors, staged with it (column passes)
-        float2 wt1a = make_float2(1.f, 0.f), wt1b = make_float2(1.f, 0.f);
+        // this tile's first pass-weight factors w_M^(b r) (column passes): r =
+        // k1, and for D = 32 also r = k1 + 32; for D = 32 the base w_M^(b U)
+        // of the second factors
+        float2 wt1a = make_float2(1.f, 0.f), wt1b = make_float2(1.f, 0.f), wbase = make_float2(1.f, 0.f);
         if (tmaw) {
-            if constexpr (G::U_STAGED) {
-                const float2 *t1s = st + (size_t)R * W;
-                wt1a = t1s[k1 * W + w];        // r = k1
-                wt1b = t1s[(k1 + D) * W + w];  // r = k1 + D
-            } else {
-                wt1a = __ldg(reinterpret_cast<const float2 *>(p.tw_pass) + (int64_t)k1 * p.B + bcol);  // r = k1
+            const float2 *t1 = reinterpret_cast<const float2 *>(p.tw_pass);
+            wt1a = __ldg(t1 + (int64_t)k1 * p.B + bcol);
+            if constexpr (!G::STAGE_T2) {
+                wt1b = __ldg(t1 + (int64_t)(k1 + D) * p.B + bcol);
+                wbase = __ldg(reinterpret_cast<const float2 *>(p.tw_hi) + p.B + bcol);  // row j = 1
             }
         }
         // ---- digit-1 operand: per-vector power-of-two scale (FP16)
@@ -442,12 +441,28 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
             }
             tcf_mma<LOGD, BF16>(tmem, ahs, als, bhs, bls, &mbar_mma);
         }
-        // the pass weights' second factors, w_M^(b U j), while the products run
+        // the pass weights' second factors, w_M^(b U j), while the products run:
+        // staged (D = 16) or the powers of w_M^(b U) (D = 32; at most five
+        // products deep)
         float2 wt2[16];
         if (tmaw) {
-            const float2 *t2s = st + (size_t)(R + G::U_STAGED) * W;
+            if constexpr (G::STAGE_T2) {
+                const float2 *t2s = st + (size_t)R * W;
 #pragma unroll
-            for (int j = 0; j < 16; j++) wt2[j] = t2s[j * W + w];
+                for (int j = 0; j < 16; j++) wt2[j] = t2s[j * W + w];
+            } else {
+                wt2[0] = make_float2(1.f, 0.f);
+                wt2[1] = wbase;
+                wt2[2] = c_mul(wbase, wbase);
+                wt2[4] = c_mul(wt2[2], wt2[2]);
+                wt2[8] = c_mul(wt2[4], wt2[4]);
+                wt2[3] = c_mul(wt2[2], wt2[1]);
+                wt2[5] = c_mul(wt2[4], wt2[1]);
+                wt2[6] = c_mul(wt2[4], wt2[2]);
+                wt2[7] = c_mul(wt2[4], wt2[3]);
+#pragma unroll
+                for (int j = 9; j < 16; j++) wt2[j] = c_mul(wt2[8], wt2[j - 8]);
+            }
         }
         if (!tc::mbar_wait_sleep(&mbar_mma, mma_phase, kTcWaitPolls, kTcfSleepNs)) failed = true;
         mma_phase ^= 1u;
