@@ -96,8 +96,10 @@ int fft_plan(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype dt, fft_dir di
  * schedule == NULL or "" picks the built-in heuristic (or a cached
  * autotuner choice): one pass up to 2^12 points; beyond, complex64 takes the
  * split measured fastest on GB300 for its length (passes of at most 2^10
- * points, a third pass from 2^21) and complex128 balanced passes of at most
- * 2^11; a few small complex128 transforms (n * batch <= 2^15) take two
+ * points, a third pass from 2^21); complex128 from 2^16 to 2^22 a first
+ * pass of n / 2^12 points and a last of 2^12 (also measured fastest),
+ * otherwise balanced passes of at most 2^11; a few small complex128
+ * transforms (n * batch <= 2^15) take two
  * passes of narrow tiles, spreading FP64 work over more SMs.  "auto" runs
  * the autotuner now (times candidate
  * schedules on the plan's own buffers, then caches the winner).  Otherwise

@@ -217,6 +217,18 @@ static int default_schedule(Schedule &s, int64_t n, fft_dtype dt)
         }
         return finish_schedule(s, dt, nullptr);
     }
+    // complex128 from 2^16 to 2^22: a last pass of 2^12 points (a tile of
+    // three radix-16 digits: its weights between digits are spread over 12
+    // stages) after a first pass of 2^4..2^10.  Measured on GB300 against
+    // the balanced split (forward, n batch = 2^26): 2^16 6.62 / 6.67 ms,
+    // 2^18 7.51 / 7.63, 2^20 8.36 / 8.46, 2^22 9.69 / 9.99; a first pass of
+    // 2^12 (one column per tile) is slower (2^20 as 12,8: 8.88 ms).
+    if (dt == FFT_C128 && s.t >= 16 && s.t <= 22) {
+        s.npass = 2;
+        s.pass[0].log_r = s.t - 12;
+        s.pass[1].log_r = 12;
+        return finish_schedule(s, dt, nullptr);
+    }
     // otherwise balanced passes of at most 2^11 (complex128: FP64-bound, the
     // split matters little) / 2^10 (complex64) points
     const int mt = dt == FFT_C128 ? 11 : 10;

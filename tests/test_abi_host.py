@@ -110,7 +110,8 @@ def test_default_schedule_covers_all_stages(t, dt):
 def test_default_schedule_splits():
     """One pass up to 2^12 points; complex64 beyond takes the split measured
     fastest on GB300 (column tiles of at least 4 columns, a third pass from
-    2^21); complex128 balanced passes of at most 2^11."""
+    2^21); complex128 from 2^16 to 2^22 a first pass of t - 12 and a last of
+    12, otherwise balanced passes of at most 2^11."""
     c64 = {13: [7, 6], 14: [7, 7], 15: [7, 8], 16: [8, 8], 17: [8, 9], 18: [8, 10], 19: [9, 10],
            20: [10, 10], 21: [7, 7, 7], 22: [7, 7, 8], 23: [7, 8, 8], 24: [8, 8, 8]}
     for t in range(0, 31):
@@ -120,6 +121,8 @@ def test_default_schedule_splits():
                 assert radices == [t], (t, dt)
             elif dt == M.FFT_C64 and t in c64:
                 assert radices == c64[t], t
+            elif dt == M.FFT_C128 and 16 <= t <= 22:
+                assert radices == [t - 12, 12], t
             else:
                 cap = 11 if dt == M.FFT_C128 else 10
                 g = -(-t // cap)
