@@ -985,7 +985,7 @@ def extra_configs(M, torch, dev, stream):
         eb = 16 if f64 else 8
         gen = torch.Generator(device=dev).manual_seed(14)
         rho = torch.randn(1 << nq, 1 << nq, dtype=tdt, device=dev, generator=gen)
-        for qubits in ([0], [13], [1, 12]):
+        for qubits in ([0], [13], [1, 12], [1, 6, 12]):
             q = len(qubits)
             u = np.linalg.qr(np.random.default_rng(q).standard_normal((1 << q, 1 << q)))[0].astype(np.complex128)
             ms = _time(torch, stream, lambda: M.dm_gate(rho, qubits, u, stream), 10)

@@ -309,12 +309,12 @@ int fft_tune_candidates(int64_t n, fft_dtype dt, fft_form form, char *buf, int64
  *            its element size; 1 <= n_qubits <= 15.
  *   qubits   host array of q distinct qubit numbers, bit positions counted
  *            from the right (0 <= qubit < n_qubits); their order does not
- *            matter.  q = 1 or 2.
+ *            matter.  q = 1, 2 or 3.
  *   u        host pointer to the 2^q x 2^q gate, row-major, same dtype; bit
  *            q-1 of its row/column index is the highest gated qubit.
  * Asynchronous on cuda_stream (NULL: the default stream).  Errors:
  * FFT_ERR_ARG (NULL pointers, host or misaligned rho, bad n or qubits),
- * FFT_ERR_DTYPE, FFT_ERR_UNSUPPORTED (q > 2, n > 15), FFT_ERR_CUDA. */
+ * FFT_ERR_DTYPE, FFT_ERR_UNSUPPORTED (q > 3, n > 15), FFT_ERR_CUDA. */
 int dm_gate(void *rho, int n_qubits, const int *qubits, int q, const void *u, fft_dtype dt,
             void *cuda_stream);
 

@@ -1945,7 +1945,7 @@ extern "C" int dm_gate(void *rho, int n, const int *qubits, int q, const void *u
     int st = dm_check(n, qubits, q);
     if (st != FFT_OK) return st;
     if (!u) return fail(FFT_ERR_ARG, "u is NULL");
-    if (q > 2) return fail(FFT_ERR_UNSUPPORTED, "gates on %d qubits: the kernel takes 1 or 2", q);
+    if (q > 3) return fail(FFT_ERR_UNSUPPORTED, "gates on %d qubits: the kernels take 1, 2 or 3", q);
     if (n > 15) return fail(FFT_ERR_UNSUPPORTED, "n_qubits = %d: the kernel takes up to 15", n);
     st = check_device_ptr(rho, elem_bytes(dt), "rho");
     if (st != FFT_OK) return st;

@@ -13,14 +13,18 @@
 // has row I with zero bits inserted at the gated positions, plus the gated
 // pattern of g (a table of 2^q offsets), and the same for the column.  One
 // thread owns one block: it reads the block's elements, applies U B U^H in
-// registers and writes them back in place.  Consecutive threads take
+// registers (one or two qubits; three go through shared memory, below) and
+// writes them back in place.  Consecutive threads take
 // consecutive column blocks J, so when qubit 0 is not gated each load and
 // store instruction of a warp covers consecutive addresses.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "codelets.cuh"
 #include "internal.h"
+#include "kernel_setup.cuh"
 
 namespace moafft {
 
@@ -101,6 +105,69 @@ __global__ void __launch_bounds__(256) dm_gate_kernel(const DmArgs<T, Q> a)
     }
 }
 
+// Gates on three qubits: a block is 8 x 8, too many values for one thread's
+// registers, so C = B U^H is formed row by row into shared memory (element
+// (g, y) of every thread's C at [(g 8 + y) threads + thread]: consecutive
+// threads, consecutive words) and U C column by column, each output column
+// stored as soon as it is complete.
+constexpr int kDm3Threads = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kDm3Threads) dm_gate3_kernel(const DmArgs<T, 3> a)
+{
+    using V = typename cvec<T>::type;
+    constexpr int M = 8;
+    extern __shared__ __align__(16) unsigned char dm_smem[];
+    V *cbuf = reinterpret_cast<V *>(dm_smem);  // M * M * kDm3Threads
+    const int nb_log = a.n - 3;
+    const int64_t blocks = ((int64_t)1) << (2 * nb_log);
+    const int64_t N = ((int64_t)1) << a.n;
+    const int tid = threadIdx.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + tid; k < blocks; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t J = k & ((((int64_t)1) << nb_log) - 1);
+        const int64_t I = k >> nb_log;
+        const int64_t r0 = spread<3>(I, a.gated), c0 = spread<3>(J, a.gated);
+        // C[g][y] = sum_d B[g][d] conj(U[y][d]), row g from row g of B
+#pragma unroll 1
+        for (int g = 0; g < M; g++) {
+            V brow[M];
+            const int64_t row = (r0 | a.off[g]) * N;
+#pragma unroll
+            for (int h = 0; h < M; h++) brow[h] = a.rho[row + (c0 | a.off[h])];
+#pragma unroll
+            for (int y = 0; y < M; y++) {
+                V c{T(0), T(0)};
+#pragma unroll
+                for (int d = 0; d < M; d++) {
+                    const V w = a.u[y * M + d];
+                    c.x += brow[d].x * w.x + brow[d].y * w.y;
+                    c.y += brow[d].y * w.x - brow[d].x * w.y;
+                }
+                cbuf[(g * M + y) * kDm3Threads + tid] = c;
+            }
+        }
+        // out[x][y] = sum_g U[x][g] C[g][y], column y at a time
+#pragma unroll 1
+        for (int y = 0; y < M; y++) {
+            V ccol[M];
+#pragma unroll
+            for (int g = 0; g < M; g++) ccol[g] = cbuf[(g * M + y) * kDm3Threads + tid];
+            const int64_t col = c0 | a.off[y];
+#pragma unroll
+            for (int x = 0; x < M; x++) {
+                V o{T(0), T(0)};
+#pragma unroll
+                for (int g = 0; g < M; g++) {
+                    const V w = a.u[x * M + g];
+                    o.x += w.x * ccol[g].x - w.y * ccol[g].y;
+                    o.y += w.x * ccol[g].y + w.y * ccol[g].x;
+                }
+                a.rho[(r0 | a.off[x]) * N + col] = o;
+            }
+        }
+    }
+}
+
 template <typename T, int Q>
 cudaError_t launch_q(void *rho, int n, const int *qubits, const void *u, cudaStream_t s)
 {
@@ -132,6 +199,15 @@ cudaError_t launch_q(void *rho, int n, const int *qubits, const void *u, cudaStr
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
+    if constexpr (Q == 3) {
+        constexpr size_t smem = (size_t)64 * kDm3Threads * sizeof(V);
+        static DeviceOnce setup;
+        cudaError_t e = smem_setup(setup, dm_gate3_kernel<T>, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::min<int64_t>((blocks + kDm3Threads - 1) / kDm3Threads, (int64_t)sms * 16);
+        dm_gate3_kernel<T><<<(unsigned)std::max<int64_t>(grid, 1), kDm3Threads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     const int64_t grid = std::min<int64_t>((blocks + 255) / 256, (int64_t)sms * 8);
     dm_gate_kernel<T, Q><<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -143,6 +219,7 @@ cudaError_t launch_dm_gate(void *rho, int n, const int *qubits, int q, const voi
 {
     if (q == 1) return f64 ? launch_q<double, 1>(rho, n, qubits, u, s) : launch_q<float, 1>(rho, n, qubits, u, s);
     if (q == 2) return f64 ? launch_q<double, 2>(rho, n, qubits, u, s) : launch_q<float, 2>(rho, n, qubits, u, s);
+    if (q == 3) return f64 ? launch_q<double, 3>(rho, n, qubits, u, s) : launch_q<float, 3>(rho, n, qubits, u, s);
     return cudaErrorNotSupported;
 }
 

@@ -1,8 +1,9 @@
 """Density-matrix gating on the GPU (dm_gate through the C ABI) against the
 FP64 oracle (Ch. "Density Matrix Operations for a Quantum Computer"): every
-qubit set of small matrices, both dtypes, and sampled blocks of a large
-matrix.  Tolerances: complex128 1e-13, complex64 2e-6 (relative to the
-largest element; each output element is a sum of 2^(2q) products)."""
+qubit set of one, two and three qubits of small matrices, both dtypes, and
+sampled blocks of a large matrix.  Tolerances: complex128 1e-13, complex64
+2e-6 (relative to the largest element; each output element is a sum of
+2^(2q) products)."""
 import itertools
 
 import numpy as np
@@ -42,7 +43,7 @@ def run(rho, qubits, u, f64):
 def test_every_qubit_set(n, f64):
     rng = np.random.default_rng(40 + n)
     N = 1 << n
-    for q in (1, 2):
+    for q in (1, 2, 3):
         for qubits in itertools.combinations(range(n), q):
             rho = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
             u = unitary(1 << q, rng)
@@ -72,7 +73,7 @@ def test_large_matrix_sampled_blocks():
     N = 1 << n
     rng = np.random.default_rng(9)
     rho = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex128)
-    for qubits in ([0], [12], [3, 9]):
+    for qubits in ([0], [12], [3, 9], [1, 6, 11]):
         u = unitary(1 << len(qubits), rng)
         t = torch.from_numpy(rho).cuda()
         M.dm_gate(t, qubits, u)
@@ -99,7 +100,7 @@ def test_large_matrix_sampled_blocks():
 
 def test_gate_errors():
     t = torch.zeros(16, 16, dtype=torch.complex64, device="cuda")
-    for qubits, status in [([0, 1, 2], M.FFT_ERR_UNSUPPORTED), ([4], M.FFT_ERR_ARG), ([1, 1], M.FFT_ERR_ARG)]:
+    for qubits, status in [([0, 1, 2, 3], M.FFT_ERR_UNSUPPORTED), ([4], M.FFT_ERR_ARG), ([1, 1], M.FFT_ERR_ARG)]:
         with pytest.raises(M.MoaFFTError) as e:
             M.dm_gate(t, qubits, np.eye(1 << len(qubits)))
         assert e.value.status == status
