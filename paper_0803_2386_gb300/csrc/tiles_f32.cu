@@ -2,6 +2,7 @@
 // tile kernel for float arithmetic (tiles of 2^4 .. 2^12 points).
 #include "bulk_kernel.cuh"
 #include "kernel_setup.cuh"
+#include "shfl_tile.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -149,6 +150,18 @@ static cudaError_t launch_tile_dir(const PassArgs &a, cudaStream_t s)
 
 cudaError_t launch_tile_f32(const PassArgs &a, int dir, cudaStream_t s)
 {
+    // single-pass tiles of 256 points: the exchange between their two
+    // digits by warp shuffles (shfl_tile.cuh); MOAFFT_NO_SHFL selects the
+    // staged tiles below (comparison)
+    static const bool shfl = getenv("MOAFFT_NO_SHFL") == nullptr;
+    if (shfl && a.log_r == 8 && a.is_last && a.A == 1 && a.col_shift == 0 && a.col_prev == 0) {
+        const int64_t ctas = (a.count + kShflRowsPerCta - 1) / kShflRowsPerCta;
+        if (ctas > 0) {
+            if (dir < 0) shfl_tile_kernel<-1><<<(unsigned)ctas, 256, 0, s>>>(a);
+            else shfl_tile_kernel<1><<<(unsigned)ctas, 256, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
     // TMA-staged form: row tiles (the last pass) by one bulk copy per row,
     // column tiles by 2-D tensor-map boxes; dense, 16-byte aligned input
     static const bool bulk = getenv("MOAFFT_NO_BULK") == nullptr;
