@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other forms (df64, precision, uneven, adjoint)")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
-    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "tc32", "c128", "df64", "dm", "nd2d"],
+    ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "tc32", "c64_256", "c128", "df64", "dm", "nd2d"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
     ap.add_argument("--extra", action="store_true",
@@ -692,7 +692,9 @@ def extra_configs(M, torch, dev, stream):
     import numpy as np
     import workloads as W
     torch.manual_seed(0)  # every synthetic input below is seeded
-    hbm = load_peaks()["hbm_gbs"]
+    peaks = load_peaks()
+    hbm = peaks["hbm_gbs"]
+    frac_key = f"hbm_frac_of_{peaks['source']}"
 
     def rel(a, b):
         return (torch.linalg.vector_norm((a.to(torch.complex128) - b).flatten()) /
@@ -751,7 +753,7 @@ def extra_configs(M, torch, dev, stream):
         gbs = 2 * n * batch * 8 / (ms * 1e-3) / 1e9
         _emit({"config": f"c64 {name} n=2^16 batch 4096 forward", "ms": round(ms, 3),
                "gflops": round(fl / (ms * 1e-3) / 1e9, 1), "gbs": round(gbs, 1),
-               "hbm_frac_of_measured": round(gbs / hbm, 4) if hbm else None,
+               frac_key: round(gbs / hbm, 4),
                "rel_err_vs_fp64": rel(out, ref), "speedup_vs_fp64": round(ms64 / ms, 2),
                "tolerance": 1e-6 * 16 if form == M.FFT_FORM_PLAIN else 1e-5 * 16})
         pf.close()
@@ -994,7 +996,7 @@ def extra_configs(M, torch, dev, stream):
             flops = elems / (1 << (2 * q)) * 2 * (1 << (3 * q)) * 8
             _emit({"config": f"density-matrix gate, {nq} qubits, qubits {qubits}, {'c128' if f64 else 'c64'}",
                    "ms": round(ms, 3), "gbs": round(gbs, 1),
-                   "hbm_frac_of_measured": round(gbs / hbm, 4) if hbm else None,
+                   frac_key: round(gbs / hbm, 4),
                    "gflops": round(flops / (ms * 1e-3) / 1e9, 1)})
         del rho
 
@@ -1037,7 +1039,7 @@ def run_case(args):
         print("ok")
         return 0
     form = {"c64": M.FFT_FORM_PLAIN, "tc_fp16": M.FFT_FORM_TC_FP16, "tc_bf16": M.FFT_FORM_TC_BF16,
-            "tc32": M.FFT_FORM_TC_FP16,
+            "tc32": M.FFT_FORM_TC_FP16, "c64_256": M.FFT_FORM_PLAIN,
             "c128": M.FFT_FORM_PLAIN, "df64": M.FFT_FORM_DF64, "c64_cluster": M.FFT_FORM_PLAIN,
             "c64_rows": M.FFT_FORM_PLAIN, "c1": M.FFT_FORM_PLAIN}[args.case]
     if args.case == "c1":  # one complex128 transform of 2^10 points (latency)
@@ -1047,6 +1049,11 @@ def run_case(args):
         p = M.Plan(n, batch, M.FFT_C128, M.FFT_FORWARD, form)
     elif args.case == "c64_rows":  # single-pass transforms (row tiles only)
         n, batch = 1 << 10, 1 << 16
+        x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form)
+    elif args.case == "c64_256":  # single-pass complex64 transforms of 256 points (warp-shuffle tiles), 256 MiB
+        n, batch = 256, 1 << 17
         x = torch.randn(batch, n, dtype=torch.complex64, device="cuda")
         y = torch.empty_like(x)
         p = M.Plan(n, batch, M.FFT_C64, M.FFT_FORWARD, form)
