@@ -1335,6 +1335,9 @@ static int exec_class(fft_plan_t p, const SizeClass &C, const void *in, void *ou
             a.err = (int *)p->err.ptr;
             a.tc_dft = p->tcf.ptr ? (const char *)p->tcf.ptr + (sign < 0 ? 0 : 4096) : nullptr;
             a.tc_dft32 = p->tcf.ptr ? (const char *)p->tcf.ptr + 8192 + (sign < 0 ? 0 : 16384) : nullptr;
+            // the double-float form keeps its (hi, lo) pairs in the workspace
+            a.df_in = p->form == FFT_FORM_DF64 && i > 0;
+            a.df_out = p->form == FFT_FORM_DF64 && i < S.npass - 1;
             fft_plan_s::Rec rec{i, nullptr, nullptr};
             if (p->profile) {
                 rec.a = take_event(p);

@@ -13,8 +13,31 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
 
 namespace moafft {
+
+// The last pass's scale (1, or 1/n for an inverse: always a power of two)
+// tested and converted with integer operations.  Done in FP64, the test and
+// the conversion to float would queue every warp on the slow FP64 pipe at
+// the start of its store phase.
+__device__ __forceinline__ bool scale_is_one(double s)
+{
+    return __double_as_longlong(s) == 0x3FF0000000000000LL;
+}
+// s = +-2^k, -126 <= k <= 127
+template <typename T>
+__device__ __forceinline__ T scale_as(double s)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        const uint32_t h = (uint32_t)__double2hiint(s);
+        return __uint_as_float((h & 0x80000000u) | ((((h >> 20) & 0x7FFu) - 896u) << 23));
+    } else {
+        return (T)s;
+    }
+}
 
 template <typename T> struct cvec;
 template <> struct cvec<float> { using type = float2; };

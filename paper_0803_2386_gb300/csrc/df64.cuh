@@ -7,14 +7,23 @@
 // double-float form keeps complex128 as the HBM format and the FP64 level of
 // accuracy (a few 1e-15 per operation) while running the butterflies in
 // FP32 instructions:
-//   sum:     Knuth's TwoSum of the high parts, plus the low parts, then a
-//            renormalising fast-two-sum (11 FP32 operations);
+//   sum:     Knuth's TwoSum of the high parts; the low parts and the
+//            TwoSum error are added into lo (8 FP32 operations);
 //   product: the exact product of the high parts from one FMA (the rounding
-//            error of a*b is fma(a, b, -a*b)), plus the two cross terms,
-//            renormalised (7 operations).
+//            error of a*b is fma(a, b, -a*b)), plus the two cross terms
+//            (4 operations).
+// Neither renormalises its result: lo may grow to a few units of hi's last
+// place over a chain of operations, which costs nothing in accuracy for a
+// linear transform whose error is measured against the norm of its data (a
+// product's cross term lo*b.hi is still formed in FP32 to 2^-24 of a term
+// that is itself 2^-22 of the value).  df_norm (a fast-two-sum, 3
+// operations) brings |lo| back below half a unit of hi; the tile kernels
+// apply it where a value leaves the registers (shared-memory exchanges,
+// stores), so no chain spans more than one radix-16 digit.
 // The conversions at the HBM boundary -- double -> (hi, lo) on load and
-// (hi, lo) -> double on store -- are done with integer bit operations, so no
-// FP64 instruction is issued anywhere on the path.
+// (hi, lo) -> double on store -- are done with integer bit operations and
+// exact FP32 scalings, so no FP64 instruction is issued anywhere on the
+// path.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,9 +51,8 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b)
 {
     const float s = a.hi + b.hi;
     const float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e += a.lo + b.lo;
-    return df_fast_two_sum(s, e);
+    const float t = (a.hi - (s - bb)) + (b.hi - bb);  // a.hi + b.hi = s + t exactly
+    return dfloat(s, t + (a.lo + b.lo));
 }
 
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
@@ -56,8 +64,10 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b)
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
+    return dfloat(p, e);
 }
+
+__device__ __forceinline__ dfloat df_norm(dfloat a) { return df_fast_two_sum(a.hi, a.lo); }
 
 struct dcplx {
     dfloat x, y;
@@ -73,8 +83,8 @@ template <> struct cvec<dfloat> { using type = dcplx; };
 // (resolution 2^-149), and a double below FP32's normal range becomes a
 // subnormal hi (truncated) with lo = 0: precision fades out gradually down
 // to 2^-149, below which a value becomes 0.  Doubles beyond FP32's range
-// become infinite.  Integer operations only.  The rare cases sit in
-// functions of their own, so the code inlined at every load stays short.
+// become infinite.  No FP64 instruction.  The general and rare cases sit
+// in functions of their own, so the code inlined at every load stays short.
 static __device__ __noinline__ dfloat df_from_double_rare(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -97,7 +107,7 @@ static __device__ __noinline__ dfloat df_from_double_rare(double x)
     return dfloat(hi, __uint_as_float(sgn | (f & 0x7FFFFFu)));
 }
 
-__device__ __forceinline__ dfloat df_from_double(double x)
+static __device__ __noinline__ dfloat df_from_double_general(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const uint32_t sgn = (uint32_t)(b >> 63) << 31;
@@ -114,8 +124,26 @@ __device__ __forceinline__ dfloat df_from_double(double x)
     return dfloat(hi, __uint_as_float(sgn | ((uint32_t)el << 23) | frac));
 }
 
+// The conversion inlined at every load, for 2^-74 <= |x| < 2^128 (the rest
+// goes to df_from_double_general).  hi: the double's pattern shifted right
+// by 29 bits keeps the top 23 fraction bits and the low 9 exponent bits; a
+// rebias by +128 modulo 256 turns the latter into FP32's exponent field.
+// lo: the 29 remaining bits as an integer r, converted truncating (24
+// significant bits, as above) and scaled by the power of two 2^(e - 1075),
+// which is a normal float in this range, so the product is exact.
+__device__ __forceinline__ dfloat df_from_double(double x)
+{
+    const uint32_t H = (uint32_t)__double2hiint(x), L = (uint32_t)__double2loint(x);
+    const uint32_t e = (H >> 20) & 0x7FFu;
+    if (e - 949u > 201u) return df_from_double_general(x);
+    const uint32_t sg = H & 0x80000000u;
+    const float hi = __uint_as_float(((__funnelshift_r(L, H, 29) + 0x40000000u) & 0x7FFFFFFFu) | sg);
+    const float sc = __uint_as_float(((e - 948u) << 23) | sg);
+    return dfloat(hi, __uint2float_rz(L & 0x1FFFFFFFu) * sc);
+}
+
 // hi + lo rounded toward zero to a double (|lo| < ulp(hi) assumed, which
-// every operation above guarantees); subnormal floats count with their value
+// df_norm guarantees); subnormal floats count with their value
 // (hi subnormal: the double holds it exactly, lo is then below 2^-149 and
 // 0).  The significand sum of hi and a (normal or subnormal) lo.
 __device__ __forceinline__ double df_to_double_sum(uint32_t bh, uint32_t bl, int eh, int el)
@@ -164,7 +192,7 @@ static __device__ __noinline__ double df_to_double_rare(uint32_t bh, uint32_t bl
     return df_to_double_sum(bh, el == 0xff ? 0u : bl, eh, el == 0xff ? 0 : el);
 }
 
-__device__ __forceinline__ double df_to_double(dfloat v)
+static __device__ __noinline__ double df_to_double_general(dfloat v)
 {
     const uint32_t bh = __float_as_uint(v.hi), bl = __float_as_uint(v.lo);
     const int eh = (int)((bh >> 23) & 0xff);
@@ -173,7 +201,30 @@ __device__ __forceinline__ double df_to_double(dfloat v)
     return df_to_double_sum(bh, bl, eh, el);
 }
 
+// The conversion inlined at every store, for a normalised value (|lo| <=
+// ulp(hi) / 2, df_norm) with 2^-75 <= |hi| < 2^128 (the rest goes to
+// df_to_double_general): hi widened to a double exactly, plus lo counted in
+// units of the double's last place at hi's binade -- lo 2^(179 - eh), at
+// most 2^28 in magnitude, rounded to the nearest integer, with hi's sign
+// folded in so that adding it to the pattern works on magnitudes.  A
+// normalised lo cannot carry the sum into the next binade; where hi is a
+// power of two and lo points toward zero the units below hi's binade are
+// half as large, so the count doubles.
+__device__ __forceinline__ double df_to_double(dfloat v)
+{
+    const uint32_t bh = __float_as_uint(v.hi);
+    const uint32_t ex = bh & 0x7F800000u;
+    const float sc = __uint_as_float(((306u << 23) - ex) | (bh & 0x80000000u));
+    int li = __float2int_rn(v.lo * sc);
+    if ((ex >> 23) - 52u > 202u) return df_to_double_general(v);
+    if ((bh & 0x7FFFFFu) == 0 && li < 0) li *= 2;
+    const uint32_t top = (((bh & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (bh & 0x80000000u);
+    const unsigned long long bits = ((((unsigned long long)top) << 32) | (unsigned long long)(bh << 29)) + (long long)li;
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ dcplx dc_from(double2 a) { return dcplx{df_from_double(a.x), df_from_double(a.y)}; }
-__device__ __forceinline__ double2 dc_to(dcplx a) { return make_double2(df_to_double(a.x), df_to_double(a.y)); }
+// a normalised on the way out
+__device__ __forceinline__ double2 dc_to(dcplx a) { return make_double2(df_to_double(df_norm(a.x)), df_to_double(df_norm(a.y))); }
 
 }  // namespace moafft

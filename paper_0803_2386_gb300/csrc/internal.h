@@ -117,6 +117,10 @@ struct PassArgs {
     // same for the 32-point DFT (64x64 reals, 2 x 8192 bytes)
     const void *tc_dft;
     const void *tc_dft32;
+    // double-float form: this pass reads (df_in) / writes (df_out) the
+    // workspace between passes as (hi, lo) float pairs -- 16 bytes a point,
+    // like complex128, without the conversions -- instead of complex128
+    int df_in, df_out;
 };
 
 // One segment of a persistent launch: tickets [first, first + nctas) are the

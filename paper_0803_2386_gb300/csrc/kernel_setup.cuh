@@ -16,19 +16,32 @@ inline cudaError_t current_device(int *dev)
     return e;
 }
 
-// Allow `smem` bytes of dynamic shared memory and prefer the largest
-// shared-memory carveout for `kernel`, once per device.
+// Allow `smem` bytes of dynamic shared memory for `kernel`, once per
+// device, and prefer the largest shared-memory carveout -- or, with ctas >
+// 0, the carveout that holds `ctas` resident CTAs, so that the rest of the
+// SM's unified L1 / shared memory stays L1 (for weight tables read through
+// L1).
 template <typename K>
-cudaError_t smem_setup(DeviceOnce &d, K kernel, size_t smem)
+cudaError_t smem_setup(DeviceOnce &d, K kernel, size_t smem, int ctas = 0)
 {
     int dev = 0;
     cudaError_t e = current_device(&dev);
     if (e != cudaSuccess) return e;
-    const int code = device_once(d, dev, nullptr, [&](int, long long *) -> int {
+    const int code = device_once(d, dev, nullptr, [&](int devno, long long *) -> int {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
+        int carve = (int)cudaSharedmemCarveoutMaxShared;
+        if (r == cudaSuccess && ctas > 0) {
+            cudaFuncAttributes fa;
+            int smem_sm = 0, resv = 0;
+            r = cudaFuncGetAttributes(&fa, kernel);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, devno);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, devno);
+            if (r == cudaSuccess && smem_sm > 0) {
+                const size_t need = (size_t)ctas * (smem + fa.sharedSizeBytes + (size_t)resv);
+                carve = (int)std::min<size_t>(100, (need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm);
+            }
+        }
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
         return (int)r;
     });
     return code < 0 ? cudaErrorInvalidDevice : (cudaError_t)code;

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
             __syncthreads();
         }
         const int64_t stride_k = n / R;  // (n/R)*k
-        const T sc = (T)p.scale;
+        const T sc = scale_as<T>(p.scale);
         for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
             int w = idx % W, k = idx / W;
             int64_t tr, v_row;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) pass_kernel(PassArgs p)
             else { tr = tr0 + w; v_row = 0; }
             if (tr >= p.count) continue;
             V v = tile[spad(tile_pos(k, p) * W + w)];
-            if (p.scale != 1.0) { v.x *= sc; v.y *= sc; }
+            if (!scale_is_one(p.scale)) { v.x *= sc; v.y *= sc; }
             out[(p.out_off ? p.out_off[tr] : tr * n) + v_row + stride_k * k] = v;
         }
     }

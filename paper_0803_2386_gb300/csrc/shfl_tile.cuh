@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(256) shfl_tile_kernel(PassArgs p)
     shfl_round<1>(v, lane);
     dft_codelet<DIR, 4>(v);
     if (!valid) return;
-    const float sc = (float)p.scale;
-    const bool scale = p.scale != 1.0;
+    const float sc = scale_as<float>(p.scale);
+    const bool scale = !scale_is_one(p.scale);
 #pragma unroll
     for (int k2 = 0; k2 < 16; k2++) {
         float2 x = v[k2];

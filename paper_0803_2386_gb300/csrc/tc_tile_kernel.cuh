@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(tile_threads(LOGR), 2) tc_tile_kernel(PassArgs
     } else {
         const int64_t obase = sbase + vrow;
         const int64_t kstride = n / R;
-        const float sc = (float)p.scale;
-        const bool scale = p.scale != 1.0;
+        const float sc = scale_as<float>(p.scale);
+        const bool scale = !scale_is_one(p.scale);
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int kk = revu + U * j;

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(128, LOGD == 4 ? 4 : 2)
             tcf_issue<LOGD, LAST>(p, &maps, tmaw, t + 2 * GS, stage + buf * SE, &mbar_st[buf]);
         }
         // ---- this thread's outputs out[k1 + D k2], k2 < D
-        const float u2 = ldexpf(1.f, e2) * (LAST ? (float)p.scale : 1.f);
+        const float u2 = ldexpf(1.f, e2) * (LAST ? scale_as<float>(p.scale) : 1.f);
         if (valid) {
             if constexpr (!LAST) {
 #pragma unroll

@@ -67,11 +67,14 @@ __device__ __forceinline__ int tpad(int pos) { return pos + (pos >> 4); }
 template <typename T> struct MemOf {
     using V = typename cvec<T>::type;
     using E = V;
-    static __device__ __forceinline__ V load(const E *p) { return *p; }
-    static __device__ __forceinline__ void store(E *p, V v) { *p = v; }
+    // raw: the double-float form's (hi, lo) pairs between passes (PassArgs::df_in / df_out)
+    static __device__ __forceinline__ V load(const E *p, bool raw) { (void)raw; return *p; }
+    static __device__ __forceinline__ void store(E *p, V v, bool raw) { (void)raw; *p = v; }
     static __device__ __forceinline__ V ldg(const V *p) { return __ldg(p); }
+    // a value leaving the registers (shared-memory exchanges)
+    static __device__ __forceinline__ V norm(V v) { return v; }
     // f: the scale already converted to the scalar type (once per thread)
-    static __device__ __forceinline__ T prep(double s) { return (T)s; }
+    static __device__ __forceinline__ T prep(double s) { return scale_as<T>(s); }
     static __device__ __forceinline__ void scale(V &v, T f)
     {
         v.x *= f;
@@ -81,15 +84,33 @@ template <typename T> struct MemOf {
 template <> struct MemOf<dfloat> {
     using V = dcplx;
     using E = double2;
-    static __device__ __forceinline__ V load(const E *p) { return dc_from(*p); }
-    static __device__ __forceinline__ void store(E *p, V v) { *p = dc_to(v); }
+    static __device__ __forceinline__ V load(const E *p, bool raw)
+    {
+        if (raw) {
+            const float4 t = *reinterpret_cast<const float4 *>(p);
+            return dcplx{dfloat(t.x, t.y), dfloat(t.z, t.w)};
+        }
+        return dc_from(*p);
+    }
+    static __device__ __forceinline__ void store(E *p, V v, bool raw)
+    {
+        if (raw) {
+            const dfloat a = df_norm(v.x), b = df_norm(v.y);
+            *reinterpret_cast<float4 *>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
+            *p = dc_to(v);
+        }
+    }
     static __device__ __forceinline__ V ldg(const V *p)
     {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         return dcplx{dfloat(t.x, t.y), dfloat(t.z, t.w)};
     }
+    // the lazy sums and products let lo grow within a digit: renormalise
+    // where a value leaves the registers (stores normalise in dc_to)
+    static __device__ __forceinline__ V norm(V v) { return dcplx{df_norm(v.x), df_norm(v.y)}; }
     // the scale is a power of two: scaling both parts is exact
-    static __device__ __forceinline__ float prep(double s) { return (float)s; }
+    static __device__ __forceinline__ float prep(double s) { return scale_as<float>(s); }
     static __device__ __forceinline__ void scale(V &v, float f)
     {
         v.x = dfloat(v.x.hi * f, v.x.lo * f);
@@ -243,7 +264,7 @@ __device__ __forceinline__ void tile_load(const PassArgs &p, const TileRef &r, t
 #pragma unroll
         for (int e = 0; e < E0; e++) {
             const int m = e * Q0 + g * U + u;
-            if (valid) v[g * E0 + e] = M::load(in + base + (int64_t)m * mstride);
+            if (valid) v[g * E0 + e] = M::load(in + base + (int64_t)m * mstride, p.df_in);
             else { v[g * E0 + e].x = T(0.0); v[g * E0 + e].y = T(0.0); }
         }
 
@@ -298,7 +319,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
 #pragma unroll
         for (int g = 0; g < G0; g++)
 #pragma unroll
-            for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + g * U + u) * W + w] = v[g * E0 + k];
+            for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + g * U + u) * W + w] = M::norm(v[g * E0 + k]);
         __syncthreads();
         int S = Q0;
         int doff = R;  // this digit level's table
@@ -321,7 +342,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
                 doff += S;
                 // each thread rewrites exactly the positions it read
 #pragma unroll
-                for (int k = 0; k < 16; k++) tile[tpad(pos0 + k * Q) * W + w] = v[k];
+                for (int k = 0; k < 16; k++) tile[tpad(pos0 + k * Q) * W + w] = M::norm(v[k]);
                 __syncthreads();
             }
             S = Q;
@@ -353,14 +374,14 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     }
     if constexpr (LAST && STAGE > 0) {
         __syncthreads();  // every thread has finished with the exchange tile
-        const bool scale = p.scale != 1.0;
+        const bool scale = !scale_is_one(p.scale);
         const auto sf = M::prep(p.scale);
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             V x = v[j];
             if (scale) M::scale(x, sf);
             const int kk = revu + U * j;
-            tile[w * STAGE + (PADDED ? tpad(kk) : kk)] = x;
+            tile[w * STAGE + (PADDED ? tpad(kk) : kk)] = M::norm(x);
         }
         return;
     }
@@ -379,7 +400,7 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
                 const int kk = revu + U * j;
                 V x = v[j];
                 if (b != 0 && kk != 0) x = c_tw<DIR>(x, c_mul(wr, M::ldg(t1 + (int64_t)j * ld)));
-                M::store(out + sbase + (int64_t)kk * ks, x);
+                M::store(out + sbase + (int64_t)kk * ks, x, p.df_out);
             }
         } else {
 #pragma unroll
@@ -387,20 +408,20 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
                 const int kk = revu + U * j;  // NS == 1: R = 16, U = 1, revu = 0
                 V x = v[j];
                 if (p.tw_mode != kTwNone && b != 0 && kk != 0) x = c_tw<DIR>(x, pass_weight_at<T>(p, b, kk));
-                M::store(out + sbase + (int64_t)kk * ks, x);
+                M::store(out + sbase + (int64_t)kk * ks, x, p.df_out);
             }
         }
     } else {
         const int64_t obase = sbase + vrow;
         const int64_t kstride = n / R;
-        const bool scale = p.scale != 1.0;
+        const bool scale = !scale_is_one(p.scale);
         const auto sf = M::prep(p.scale);
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int kk = revu + U * j;
             V x = v[j];
             if (scale) M::scale(x, sf);
-            M::store(out + obase + (int64_t)kk * kstride, x);
+            M::store(out + obase + (int64_t)kk * kstride, x, p.df_out);
         }
     }
 }
@@ -417,6 +438,157 @@ __device__ __forceinline__ void tile_body(const PassArgs &p, const int64_t cta, 
     tile_finish<T, DIR, LOGR, LAST, W>(p, r, v, tile);
 }
 
+// this thread's natural tile indices are revu + U j (j < 16): u holds the
+// earlier digits, the first one most significant (see tile_finish)
+template <int LOGR>
+__device__ __forceinline__ int tile_revu(int u)
+{
+    constexpr int NS = (LOGR + 3) / 4;
+    constexpr int L0 = LOGR - 4 * (NS - 1);
+    int revu = 0;
+    if constexpr (NS > 1) {
+        int rem = u;
+        int digits[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = NS - 2; j >= 1; j--) {
+            digits[j] = rem & 15;
+            rem >>= 4;
+        }
+        digits[0] = rem;
+        revu = digits[0];
+        int shift = L0;
+#pragma unroll
+        for (int j = 1; j <= NS - 2; j++) {
+            revu |= digits[j] << shift;
+            shift += 4;
+        }
+    }
+    return revu;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+
+// The double-float tile of 2^(4 NS) points (NS radix-16 digits), arranged
+// so that one copy of the digit's code serves every digit: the same steps
+// as tile_load + tile_finish, with shared memory standing in for the
+// register array wherever a loop would index it.  A double-float digit is
+// about 1,300 instructions, so the unrolled form (a copy per digit, and
+// the conversions and weights of all 16 points inlined at the load and the
+// store) outgrows the instruction cache.
+//   1. HBM -> shared memory: the thread's 16 first-digit points, as raw
+//      complex128 by asynchronous 16-byte copies, all in flight at once;
+//   2. each thread converts its own points to double-float in place;
+//   3. the digits, one loop body: read 16 points, codelet, weights, write
+//      back (renormalised), barrier -- the first digit reads the thread's
+//      own points, the last leaves its results at the thread's own
+//      positions, so neither needs a barrier before it;
+//   4. stores: the thread's 16 results from shared memory, with the pass
+//      weights (non-last pass) or the scale and final transpose (last
+//      pass), converted back to complex128.
+template <int DIR, int LOGR, bool LAST, int W>
+__device__ __forceinline__ void tile_body_df(const PassArgs &p, const int64_t cta, dcplx *tile)
+{
+    using V = dcplx;
+    using M = MemOf<dfloat>;
+    constexpr int R = 1 << LOGR;
+    constexpr int NS = LOGR / 4;
+    constexpr int U = R / 16;  // threads per column
+    static_assert(LOGR % 4 == 0 && NS >= 2 && NS <= 3, "radix-16 digits");
+    const int tid = threadIdx.x;
+    const int w = tid % W;
+    const int u = tid / W;
+    const TileRef r = tile_ref<dfloat, LOGR, LAST, W>(p, cta);
+    const bool valid = r.valid;
+
+    // ---- 1. raw points m = e U + u of column w
+    {
+        const double2 *in = reinterpret_cast<const double2 *>(p.in) + r.base;
+        const int64_t mstride = LAST ? 1 : p.B;
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int m = e * U + u;
+            V *slot = &tile[tpad(m) * W + w];
+            if (valid) cp_async16(slot, in + (int64_t)m * mstride);
+            else *slot = V{};
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    }
+    // ---- 2. complex128 -> double-float, in place (not for the (hi, lo)
+    // pairs an earlier pass left in the workspace)
+    if (!p.df_in) {
+#pragma unroll 2
+        for (int e = 0; e < 16; e++) {
+            V *slot = &tile[tpad(e * U + u) * W + w];
+            *slot = dc_from(*reinterpret_cast<const double2 *>(slot));
+        }
+    }
+    // ---- 3. the radix-16 digits
+    const V *twd = reinterpret_cast<const V *>(p.tw_digit);  // weights between digits, rows by k
+    V v[16];
+    int S = R;
+    int doff = 0;  // this digit level's table
+#pragma unroll 1
+    for (int j = 0; j < NS; j++) {
+        const int Q = S / 16;
+        const int pre = u / Q, mq = u % Q;
+        const int pos0 = pre * S + mq;
+#pragma unroll
+        for (int e = 0; e < 16; e++) v[e] = tile[tpad(pos0 + e * Q) * W + w];
+        if (valid) {
+            dft_codelet<DIR, 4>(v);
+            if (j < NS - 1 && mq != 0) {
+#pragma unroll
+                for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twd + doff + k * Q + mq));
+            }
+        }
+        // each thread rewrites exactly the positions it read
+#pragma unroll
+        for (int k = 0; k < 16; k++) tile[tpad(pos0 + k * Q) * W + w] = M::norm(v[k]);
+        doff += S;
+        S = Q;
+        if (j < NS - 1) __syncthreads();
+    }
+    if (!valid) return;
+    // ---- 4. result j (tile index revu + U j) sits at position 16 u + j
+    const int revu = tile_revu<LOGR>(u);
+    M::E *out = reinterpret_cast<M::E *>(p.out);
+    if constexpr (!LAST) {
+        const int64_t b = (r.b0 + w) >> p.col_shift;  // the weights' column
+        const int64_t ks = r.kstride;
+        const int64_t ld = p.B >> p.col_shift;
+        V wr{};
+        if (p.tw_mode == 3) wr = M::ldg(reinterpret_cast<const V *>(p.tw_pass) + (int64_t)revu * ld + b);
+#pragma unroll 4
+        for (int jj = 0; jj < 16; jj++) {
+            const int kk = revu + U * jj;
+            V x = tile[tpad(16 * u + jj) * W + w];
+            if (p.tw_mode != kTwNone && b != 0 && kk != 0) {
+                const V wt = p.tw_mode == 3
+                                 ? c_mul(wr, M::ldg(reinterpret_cast<const V *>(p.tw_hi) + (int64_t)jj * ld + b))
+                                 : pass_weight_at<dfloat>(p, b, kk);
+                x = c_tw<DIR>(x, wt);
+            }
+            M::store(out + r.sbase + (int64_t)kk * ks, x, p.df_out);
+        }
+    } else {
+        const int64_t obase = r.sbase + r.vrow;
+        const int64_t kstride = p.n / R;
+        const bool scale = !scale_is_one(p.scale);
+        const float sf = M::prep(p.scale);
+#pragma unroll 4
+        for (int jj = 0; jj < 16; jj++) {
+            const int kk = revu + U * jj;
+            V x = tile[tpad(16 * u + jj) * W + w];
+            if (scale) M::scale(x, sf);
+            M::store(out + obase + (int64_t)kk * kstride, x, p.df_out);
+        }
+    }
+}
+
 template <typename T, int DIR, int LOGR, bool LAST>
 __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     tile_kernel(PassArgs p)
@@ -424,7 +596,10 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     using V = typename cvec<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
-    tile_body<T, DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));
+    if constexpr (std::is_same<T, dfloat>::value && LOGR % 4 == 0 && LOGR >= 8)
+        tile_body_df<DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));
+    else
+        tile_body<T, DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));
 }
 
 }  // namespace moafft

@@ -11,7 +11,7 @@ static cudaError_t launch_df_one(const PassArgs &a, cudaStream_t s)
     constexpr int W = tile_width(LOGR);
     constexpr size_t smem = LOGR >= 5 ? (size_t)((1 << LOGR) + (1 << LOGR) / 16) * W * sizeof(dcplx) : 0;
     static DeviceOnce setup;
-    cudaError_t e = smem_setup(setup, tile_kernel<dfloat, DIR, LOGR, LAST>, smem);
+    cudaError_t e = smem_setup(setup, tile_kernel<dfloat, DIR, LOGR, LAST>, smem, tile_min_blocks<dfloat>(LOGR));
     if (e != cudaSuccess) return e;
     int64_t ctas;
     if (!LAST) ctas = a.count * a.A * (a.B / W);
