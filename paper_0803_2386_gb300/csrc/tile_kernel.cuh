@@ -77,8 +77,13 @@ template <typename T> struct MemOf {
     static __device__ __forceinline__ T prep(double s) { return scale_as<T>(s); }
     static __device__ __forceinline__ void scale(V &v, T f)
     {
-        v.x *= f;
-        v.y *= f;
+        if constexpr (std::is_same<T, double>::value) {
+            v.x = scale_pow2(v.x, f);
+            v.y = scale_pow2(v.y, f);
+        } else {
+            v.x *= f;
+            v.y *= f;
+        }
     }
 };
 template <> struct MemOf<dfloat> {

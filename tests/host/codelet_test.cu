@@ -1,0 +1,96 @@
+// Host check of the register codelets (codelets.cuh): every radix-2^k DFT
+// codelet, in both directions, against the DFT sum X_k = sum_n x_n
+// w^(n k), w = exp(s 2 pi i / E), taken in long double; and the FP64
+// 16-point codelet with fused multiply-add butterflies (dft16_fma) against
+// the same sum and against the plain dft16.  Compiled by nvcc as host code
+// (the codelets are __host__ __device__) and run on the CPU.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "codelets.cuh"
+
+using namespace moafft;
+
+static unsigned long long g_state = 0x9E3779B97F4A7C15ull;
+static double uniform()  // splitmix64, in [-1, 1)
+{
+    unsigned long long z = (g_state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 4503599627370496.0) - 1.0;
+}
+
+static double max_err(const double2 *got, const double2 *x, int e, int dir)
+{
+    const long double pi = 3.141592653589793238462643383279502884L;
+    long double worst = 0, scale = 0;
+    for (int k = 0; k < e; k++) {
+        long double re = 0, im = 0;
+        for (int n = 0; n < e; n++) {
+            const long double th = dir * 2 * pi * (long double)((n * k) % e) / e;
+            const long double c = cosl(th), s = sinl(th);
+            re += x[n].x * c - x[n].y * s;
+            im += x[n].x * s + x[n].y * c;
+        }
+        const long double d = hypotl(got[k].x - re, got[k].y - im);
+        if (d > worst) worst = d;
+        const long double m = hypotl(re, im);
+        if (m > scale) scale = m;
+    }
+    return (double)(worst / scale);
+}
+
+template <int DIR, int LE>
+static bool check(const char *name, double tol)
+{
+    constexpr int E = 1 << LE;
+    bool ok = true;
+    for (int trial = 0; trial < 200; trial++) {
+        double2 x[E], v[E];
+        for (int n = 0; n < E; n++) {
+            x[n] = make_double2(uniform(), uniform());
+            if (trial == 0) x[n] = make_double2(n == 0 ? 1.0 : 0.0, 0.0);  // delta -> all ones
+            v[n] = x[n];
+        }
+        dft_codelet<DIR, LE>(v);
+        const double err = max_err(v, x, E, DIR);
+        if (!(err <= tol)) {
+            std::printf("%s dir %d trial %d: max error %.3e > %.1e\n", name, DIR, trial, err, tol);
+            ok = false;
+            break;
+        }
+    }
+    return ok;
+}
+
+template <int DIR>
+static bool check_fma_vs_plain()
+{
+    for (int trial = 0; trial < 200; trial++) {
+        double2 a[16], b[16];
+        for (int n = 0; n < 16; n++) a[n] = b[n] = make_double2(uniform(), uniform());
+        dft16_fma<DIR>(a);
+        dft16<DIR>(b);
+        for (int k = 0; k < 16; k++)
+            if (std::fabs(a[k].x - b[k].x) > 1e-14 || std::fabs(a[k].y - b[k].y) > 1e-14) {
+                std::printf("dft16_fma vs dft16, dir %d: bin %d differs\n", DIR, k);
+                return false;
+            }
+    }
+    return true;
+}
+
+int main()
+{
+    bool ok = true;
+    ok &= check<-1, 1>("dft2", 1e-15) && check<1, 1>("dft2", 1e-15);
+    ok &= check<-1, 2>("dft4", 1e-15) && check<1, 2>("dft4", 1e-15);
+    ok &= check<-1, 3>("dft8", 1e-15) && check<1, 3>("dft8", 1e-15);
+    ok &= check<-1, 4>("dft16 (fma)", 1e-15) && check<1, 4>("dft16 (fma)", 1e-15);
+    ok &= check_fma_vs_plain<-1>() && check_fma_vs_plain<1>();
+    if (!ok) return 1;
+    std::printf("codelets ok\n");
+    return 0;
+}
