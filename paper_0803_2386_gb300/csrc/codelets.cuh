@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -39,19 +40,43 @@ __device__ __forceinline__ T scale_as(double s)
     }
 }
 
-// x * f for the power of two f = 2^k (the last pass's scale) without an FP64
-// product, which would cost the FP64-bound kernels two slow instructions a
-// point: where x is normal and x 2^k is too, the exponent field moves by k;
-// zeros, subnormals, infinities, NaNs and results leaving the normal range
-// take the product.
-__device__ __forceinline__ double scale_pow2(double x, double f)
+// x * f for the power of two f = 2^k, -1022 <= k <= 0 (the last pass's scale 1/n),
+// with integer operations only: a product would cost the FP64-bound kernels
+// two slow FP64 instructions a point, and a product kept for the rare cases
+// would still be issued where the compiler predicates it.  Where x and
+// x 2^k are normal the exponent field moves by k; where the result (or x)
+// is subnormal the significand shifts right, rounded to nearest even --
+// IEEE multiplication by 2^k exactly; zeros, infinities and NaNs pass.
+__host__ __device__ __forceinline__ double scale_pow2(double x, double f)
 {
-    const long long b = __double_as_longlong(x);
-    const int k = (int)((__double_as_longlong(f) >> 52) & 0x7FF) - 1023;
+    unsigned long long b, fb;
+    memcpy(&b, &x, 8);
+    memcpy(&fb, &f, 8);
+    const int k = (int)((fb >> 52) & 0x7FF) - 1023;
     const int e = (int)((b >> 52) & 0x7FF);
-    if ((unsigned)(e - 1) < 2046u && (unsigned)(e + k - 1) < 2046u)
-        return __longlong_as_double(b + ((long long)k << 52));
-    return x * f;
+    unsigned long long r;
+    if (e == 2047 || k == 0) {
+        r = b;
+    } else if (e + k >= 1) {
+        r = b - ((unsigned long long)(-k) << 52);
+    } else {
+        const unsigned long long sgn = b & 0x8000000000000000ull;
+        unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+        int sh = -k;
+        if (e) {
+            m |= 1ull << 52;
+            sh = 1 - (e + k);
+        }
+        if (sh > 54) {
+            r = sgn;
+        } else {
+            const unsigned long long q = m >> sh, rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+            r = sgn | (q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0));
+        }
+    }
+    double y;
+    memcpy(&y, &r, 8);
+    return y;
 }
 
 template <typename T> struct cvec;

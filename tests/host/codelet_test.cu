@@ -2,11 +2,15 @@
 // codelet, in both directions, against the DFT sum X_k = sum_n x_n
 // w^(n k), w = exp(s 2 pi i / E), taken in long double; and the FP64
 // 16-point codelet with fused multiply-add butterflies (dft16_fma) against
-// the same sum and against the plain dft16.  Compiled by nvcc as host code
+// the same sum and against the plain dft16; and the integer power-of-two
+// scaling of the last pass (scale_pow2) bit for bit against the host's
+// IEEE multiplication by 2^k, across normal, subnormal, zero, infinite and
+// NaN inputs.  Compiled by nvcc as host code
 // (the codelets are __host__ __device__) and run on the CPU.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "codelets.cuh"
 
@@ -82,6 +86,31 @@ static bool check_fma_vs_plain()
     return true;
 }
 
+static bool check_scale()
+{
+    const double special[] = {0.0, -0.0, 1.0, -1.0, 3.0, 0.1, 1e-300, -1e-300, 2.2250738585072014e-308,
+                              4.9406564584124654e-324, 1e-310, -1e-315, 1.7976931348623157e308,
+                              INFINITY, -INFINITY, NAN};
+    int bad = 0;
+    for (int k = 0; k >= -1022; k--) {  // f = 2^k a normal double (1/n)
+        const double f = ldexp(1.0, k);
+        for (int i = 0; i < 2000; i++) {
+            double x;
+            if (i < (int)(sizeof special / sizeof special[0])) x = special[i];
+            else if (i % 3 == 0) x = ldexp(uniform(), -(int)((uniform() + 1.0) * 540.0));  // down to subnormals
+            else x = uniform() * ldexp(1.0, (int)(uniform() * 1000.0));
+            const double want = x * f, got = scale_pow2(x, f);
+            unsigned long long a, b;
+            memcpy(&a, &want, 8);
+            memcpy(&b, &got, 8);
+            if (a != b && !(std::isnan(want) && std::isnan(got))) {
+                if (bad++ < 5) std::printf("scale_pow2(%.17g, 2^%d) = %.17g, want %.17g\n", x, k, got, want);
+            }
+        }
+    }
+    return bad == 0;
+}
+
 int main()
 {
     bool ok = true;
@@ -90,6 +119,7 @@ int main()
     ok &= check<-1, 3>("dft8", 1e-15) && check<1, 3>("dft8", 1e-15);
     ok &= check<-1, 4>("dft16 (fma)", 1e-15) && check<1, 4>("dft16 (fma)", 1e-15);
     ok &= check_fma_vs_plain<-1>() && check_fma_vs_plain<1>();
+    ok &= check_scale();
     if (!ok) return 1;
     std::printf("codelets ok\n");
     return 0;
