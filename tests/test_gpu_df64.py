@@ -24,11 +24,11 @@ def gpu():
 
 
 
-def run(x, direction=M.FFT_FORWARD, adjoint=False, inplace=False, rows=None):
+def run(x, direction=M.FFT_FORWARD, adjoint=False, inplace=False, rows=None, schedule=None):
     batch, n = x.shape
     d_in = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     d_out = d_in if inplace else torch.empty_like(d_in)
-    p = M.fft_plan_ex(n, batch, M.FFT_C128, direction, M.FFT_FORM_DF64)
+    p = M.fft_plan_ex(n, batch, M.FFT_C128, direction, M.FFT_FORM_DF64, schedule)
     try:
         (M.fft_exec_adjoint if adjoint else M.fft_exec)(p, d_in, d_out)
         M.fft_plan_check(p)
@@ -50,6 +50,22 @@ def test_df64_sizes(t):
     assert err.max() <= 1e-12
     err = err_rows(run(x, inplace=True), O.fft(x, "forward", c=64))
     assert err.max() <= 1e-12
+
+
+@pytest.mark.parametrize("t,sched", [(13, "4,4,5"), (16, "8,8"), (16, "4,12"), (20, "12,8"), (22, None),
+                                     (24, "8,8,8")])
+def test_df64_pass_boundaries(t, sched):
+    """Every pass boundary of the double-float form: the first pass reads
+    complex128 and leaves (hi, lo) float pairs in the workspace, middle
+    passes read and write pairs, the last reads pairs and writes complex128
+    -- through the generic tiles (a shorter first digit, then radix-16
+    digits) and the one-loop tiles of 2^8 / 2^12 points, in either order,
+    forward and inverse."""
+    n = 1 << t
+    x = W.uniform_complex(n, 2, seed=400 + t)
+    for direction, op in ((M.FFT_FORWARD, "forward"), (M.FFT_INVERSE, "inverse")):
+        err = err_rows(run(x, direction, schedule=sched), O.fft(x, op, c=1024, threads=2))
+        assert err.max() <= 1e-12, (t, sched, op, err.max())
 
 
 def test_df64_closed_forms_n1024():
