@@ -607,15 +607,22 @@ static int64_t launches_per_exec(const fft_plan_s *p)
     return k;
 }
 
+// The digit tables' element kind (digit_table_entries): 0 complex128 FP64,
+// 1 complex64, 2 double-float.
+static int table_kind(const fft_plan_s *p)
+{
+    return p->form == FFT_FORM_DF64 ? 2 : (p->dt == FFT_C128 ? 0 : 1);
+}
+
 // Offsets (in table entries) of one pass's weight tables: the tile table
 // (R entries), the digit tables, and for passes with pass weights their
 // table(s), whose rows hold B >> col_shift columns.
-static void layout_pass_tables(PassDesc &d, bool last, size_t &off)
+static void layout_pass_tables(PassDesc &d, bool last, size_t &off, int kind)
 {
     d.tw_tile_off = off;
     off += (size_t)1 << d.log_r;
     d.tw_digit_off = off;
-    off += (size_t)digit_table_entries(d.log_r);
+    off += (size_t)digit_table_entries(d.log_r, kind);
     if (last || d.tw_mode == kTwNone) return;
     const int64_t cols = d.B >> d.col_shift;
     d.tw_pass_off = off;
@@ -638,7 +645,7 @@ static void layout_pass_tables(PassDesc &d, bool last, size_t &off)
 static cudaError_t gen_pass_tables(const fft_plan_s *p, char *arena, const PassDesc &d, bool last)
 {
     const size_t wb = p->form == FFT_FORM_DF64 ? 16 : elem_bytes(p->dt);
-    const int kind = p->form == FFT_FORM_DF64 ? 2 : (p->dt == FFT_C128 ? 0 : 1);
+    const int kind = table_kind(p);
     auto gen = [&](size_t o, int64_t count, int64_t m, int64_t stride) -> cudaError_t {
         if (p->form == FFT_FORM_DF64) return launch_twiddle_df64((float *)(arena + o * wb), count, m, stride, 0);
         if (p->dt == FFT_C128) return launch_twiddle_f64((double *)(arena + o * wb), count, m, stride, 0);
@@ -677,7 +684,8 @@ static int make_tables(fft_plan_s *p)
             c.sched.tw_direct_off = off;
             off += (size_t)c.n;
         }
-        for (int i = 0; i < c.sched.npass; i++) layout_pass_tables(c.sched.pass[i], i == c.sched.npass - 1, off);
+        for (int i = 0; i < c.sched.npass; i++)
+            layout_pass_tables(c.sched.pass[i], i == c.sched.npass - 1, off, table_kind(p));
     }
     int st = dev_alloc(p->tw, off * eb, "twiddle tables");
     if (st != FFT_OK) return st;
@@ -974,7 +982,7 @@ extern "C" int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64
             split_subpasses(q);
             q.tw_mode = kTwNone;
             q.tw_m = 1;
-            layout_pass_tables(q, false, off);
+            layout_pass_tables(q, false, off, table_kind(p));
         } else {
             Schedule s1;
             const std::string two = std::to_string((lg + 1) / 2) + "," + std::to_string(lg / 2);
@@ -998,8 +1006,8 @@ extern "C" int fft_plan_nd(fft_plan_t *out, int ndim, const int64_t *dims, int64
             ax.pass[1].col_prev = R0;
             ax.pass[1].tw_mode = kTwNone;
             ax.pass[1].width = width_for(s1.pass[1].log_r, S);
-            layout_pass_tables(ax.pass[0], false, off);
-            layout_pass_tables(ax.pass[1], false, off);
+            layout_pass_tables(ax.pass[0], false, off, table_kind(p));
+            layout_pass_tables(ax.pass[1], false, off, table_kind(p));
             ax.chunk = std::max<int64_t>(1, std::min<int64_t>(batch, target / (per * (int64_t)eb)));
             ws_need = std::max<int64_t>(ws_need, ax.chunk * per * (int64_t)eb);
         }

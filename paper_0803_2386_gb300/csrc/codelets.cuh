@@ -337,6 +337,78 @@ __host__ __device__ __forceinline__ void dft16_fma(double2 *v)
     for (int k = 0; k < 16; k++) v[k] = o[k];
 }
 
+// ---- the same network with its inputs twiddled at run time --------------
+//
+// Between two radix-16 digits of a tile every point is multiplied by a
+// weight.  For the thread that runs the later digit, the weights of its 16
+// inputs e are c w^(o e): a factor c common to all 16, which the later
+// digits can absorb as well, times a geometric sequence in e.  The DFT of
+// x_e w^(o e) is the decimation-in-time network above with every stage's
+// twiddle multiplied by a power of w^o (stage of span h: w^(o 16/2h)
+// w_2h^j), so the weights fold into its butterflies: 6 FP64 instructions
+// for each of the 32, 192 per 16 points, where a weight product per input
+// (4) and the plain codelet (148) take 208.
+//
+// The 15 twiddles T_h,j (h = 1, 2, 4, 8; j < h) come from a table, entry
+// (h - 1 + j) * ld, in the forward direction as a pair (f, r):
+//   T = f (1 + i r)        where |Re T| >= |Im T|  (f = Re T,  r = Im T / Re T),
+//   T = (f / 4) (r + i)    otherwise               (f = 4 Im T, r = Re T / Im T),
+// so |r| <= 1 and |f| >= 1/sqrt(2) in both, and |f| >= 2 marks the second
+// form.  With (a, b) = (q.re, q.im) for the first form and (q.im, q.re) for
+// the second, both forms give T q = f (t1 + i t2) from the same two FMAs,
+// t1 = a - r b and t2 = r a + b, except that the second form's t1 comes out
+// negated (DIR = +1, conjugating T: its t2) -- so instead of negating it,
+// the butterfly swaps which of its outputs takes + f t1 and which - f t1.
+// The decoding and the swaps are integer operations (exponent bits,
+// selects): a negation written in the code becomes an FP64 instruction, so
+// none is, and only the 6 fused multiply-adds reach the FP64 pipe.
+
+template <int DIR>
+__host__ __device__ __forceinline__ void bfly_fold(double2 &p, double2 &q, double f, double r, bool sinm)
+{
+    const double a = sinm ? q.y : q.x, b = sinm ? q.x : q.y;
+    const double px = p.x, py = p.y;
+    if constexpr (DIR < 0) {
+        const double t1 = fma(-r, b, a), t2 = fma(r, a, b);  // second form: t1 negated
+        const double x0 = fma(f, t1, px), x1 = fma(-f, t1, px);
+        p.x = sinm ? x1 : x0;
+        q.x = sinm ? x0 : x1;
+        p.y = fma(f, t2, py);
+        q.y = fma(-f, t2, py);
+    } else {
+        const double t1 = fma(r, b, a), t2 = fma(-r, a, b);  // second form: t2 negated
+        const double y0 = fma(f, t2, py), y1 = fma(-f, t2, py);
+        p.x = fma(f, t1, px);
+        q.x = fma(-f, t1, px);
+        p.y = sinm ? y1 : y0;
+        q.y = sinm ? y0 : y1;
+    }
+}
+
+template <int DIR>
+__host__ __device__ __forceinline__ void dft16_fma_tw(double2 *v, const double2 *tw, int ld)
+{
+#pragma unroll
+    for (int h = 1; h < 16; h *= 2)
+#pragma unroll
+        for (int j = 0; j < h; j++) {
+            const double2 fr = tw[(h - 1 + j) * ld];
+            unsigned long long fb;
+            memcpy(&fb, &fr.x, 8);
+            const bool sinm = ((fb >> 52) & 0x7FF) >= 1024;  // |f| >= 2: the second form
+            if (sinm) fb -= 2ull << 52;                       // f / 4
+            double f;
+            memcpy(&f, &fb, 8);
+#pragma unroll
+            for (int b = 0; b < 16; b += 2 * h) bfly_fold<DIR>(v[rev4(b + j)], v[rev4(b + j + h)], f, fr.y, sinm);
+        }
+    double2 o[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) o[k] = v[rev4(k)];
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = o[k];
+}
+
 template <int DIR, int LE, typename V>
 __host__ __device__ __forceinline__ void dft_codelet(V *v)
 {

@@ -204,11 +204,17 @@ cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, i
 //   level j:  Tj[k Q + mq]  = w_S^(mq k),  k < 16, mq < Q = S / 16, with
 //             S = Q0 / 16^(j-1) the sub-problem size, j = 1 .. levels - 2,
 // each level right after the previous one.
-inline int64_t digit_table_entries(int log_r)
+// For complex128 in FP64 (kind 0) the weights are instead folded into the
+// next digit's butterflies (codelets.cuh, dft16_fma_tw): per digit level j =
+// 1 .. levels - 1 and per thread u < U = R/16 of a column, its 15 stage
+// twiddles, entry (j - 1) 15 U + t U + u (fold_tables_kernel, twiddle.cu).
+// kind: 0 complex128 FP64, 1 complex64, 2 double-float.
+inline int64_t digit_table_entries(int log_r, int kind)
 {
     if (log_r < 4 || log_r > 12) return 0;
     const int ns = (log_r + 3) / 4;
     if (ns < 2) return 0;
+    if (kind == 0) return (int64_t)(ns - 1) * 15 * (((int64_t)1 << log_r) / 16);
     const int l0 = log_r - 4 * (ns - 1);
     int64_t total = (int64_t)1 << log_r;
     int64_t S = ((int64_t)1 << log_r) >> l0;

@@ -142,7 +142,7 @@ extern "C" int fft_exec_noalloc(const void *in, void *out, int64_t n, int64_t ba
         p.tw_tile_off = tables;
         tables += (size_t)R;
         p.tw_digit_off = tables;
-        tables += (size_t)digit_table_entries(p.log_r);
+        tables += (size_t)digit_table_entries(p.log_r, dt == FFT_C128 ? 0 : 1);
         p.tw_mode = 0;
         p.tw_lo_bits = 0;
         if (!last) {

@@ -19,7 +19,9 @@
 //      the reshape-transposed position k*(R/E0) + mq.
 //   3. For each further radix-16 digit: read 16 points, codelet, weights
 //      w_S^(mq*k) (S the current sub-problem size), write back -- except
-//      after the last digit, whose results stay in registers.
+//      after the last digit, whose results stay in registers.  (FP64 folds
+//      the weights of steps 2 and 3 into the next digit's butterflies
+//      instead: codelets.cuh, dft16_fma_tw.)
 //      The weights of steps 2 and 3 come from per-level tables with rows by
 //      k (digit_table_entries), so the lanes of a warp, which run over mq,
 //      read consecutive entries.
@@ -307,11 +309,15 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
     // ---- 2. first-digit codelets (threads of rows / columns beyond the
     // batch skip the arithmetic but still meet every barrier: all threads of
     // a row or column share its validity, so the exchanges stay consistent)
+    // FP64: the weights between digits are folded into the next digit's
+    // butterflies (dft16_fma_tw; the tables of fold_tables_kernel), so no
+    // digit multiplies its outputs
+    constexpr bool kFold = std::is_same<T, double>::value;
     if (valid) {
 #pragma unroll
         for (int g = 0; g < G0; g++) {
             dft_codelet<DIR, L0>(&v[g * E0]);
-            if constexpr (NS > 1) {
+            if constexpr (NS > 1 && !kFold) {
                 const int mq = g * U + u;
 #pragma unroll
                 for (int k = 1; k < E0; k++) v[g * E0 + k] = c_tw<DIR>(v[g * E0 + k], M::ldg(twd + k * Q0 + mq));
@@ -338,9 +344,12 @@ __device__ __forceinline__ void tile_finish(const PassArgs &p, const TileRef &r,
             const int pos0 = pre * S + mq;
 #pragma unroll
             for (int e = 0; e < 16; e++) v[e] = tile[tpad(pos0 + e * Q) * W + w];
-            if (valid) dft_codelet<DIR, 4>(v);
+            if (valid) {
+                if constexpr (kFold) dft16_fma_tw<DIR>(v, twd + (j - 1) * 15 * U + u, U);
+                else dft_codelet<DIR, 4>(v);
+            }
             if (j < NS - 1) {
-                if (valid && mq != 0) {
+                if (!kFold && valid && mq != 0) {
 #pragma unroll
                     for (int k = 1; k < 16; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twd + doff + k * Q + mq));
                 }

@@ -109,9 +109,56 @@ cudaError_t launch_twiddle_2d(void *dst, int kind, int64_t rows, int64_t cols, i
     return cudaGetLastError();
 }
 
+// FP64 tiles: the stage twiddles of the digits whose inputs arrive weighted
+// (tile_kernel.cuh, step 3; codelets.cuh, dft16_fma_tw).  A tile of R = E0
+// 16^(ns-1) points runs a first digit over Q_0 = R / E0 codelets, then
+// radix-16 digits j = 1 .. ns-1 over Q_j = Q_0 / 16^j codelets each.  The
+// four-step weights after digit i are w_R^(mq_i K_i ...) -- with the
+// natural index K of the outputs a point has passed through,
+//   K = k_0 + E0 (k_1 + 16 (k_2 + ...)),
+// the weight still owed by the input e of the thread u = pre Q_j + mq that
+// runs digit j (pre = k_0 16^(j-1) + ... + k_(j-1), the outputs it reads) is
+// w_R^(E), E = mq K + e Q_j K (mod R): the factor w_R^(mq K) is common to
+// the thread's 16 inputs and left for the later digits (at the last digit
+// mq = 0), the rest is the geometric sequence w^(o e), o = Q_j K, that its
+// network absorbs with the stage twiddles T_h,j' = w_R^(o 8/h + j' R/(2h)).
+// Each is stored as the pair (f, r) dft16_fma_tw reads.
+__global__ void fold_tables_kernel(double2 *dst, int log_r)
+{
+    const int ns = (log_r + 3) / 4, l0 = log_r - 4 * (ns - 1);
+    const int64_t R = (int64_t)1 << log_r, U = R / 16, E0 = (int64_t)1 << l0;
+    const int64_t count = (int64_t)(ns - 1) * 15 * U;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(idx / (15 * U)) + 1;
+        const int t = (int)((idx / U) % 15);
+        const int64_t u = idx % U;
+        const int64_t Qj = (R / E0) >> (4 * j);
+        int64_t pre = u / Qj, K = 0, place = E0;
+        for (int i = j - 1; i >= 1; i--) {  // k_(j-1) .. k_1, least significant first
+            K += (pre & 15) * (place << (4 * (i - 1)));
+            pre >>= 4;
+        }
+        K += pre;  // k_0
+        const int h = t == 0 ? 1 : t < 3 ? 2 : t < 7 ? 4 : 8;
+        const int64_t jj = t - (h - 1);
+        const int64_t o = (Qj * K) % R;
+        const int64_t e = (o * (8 / h) + jj * (R / (2 * h))) % R;
+        double sn, c;
+        sincospi(2.0 * (double)e / (double)R, &sn, &c);
+        const double d = -sn;  // forward: w_R^e = c + i d
+        dst[idx] = fabs(c) >= fabs(d) ? make_double2(c, d / c) : make_double2(4.0 * d, c / d);
+    }
+}
+
 cudaError_t launch_digit_tables(void *dst, int kind, int log_r, cudaStream_t s)
 {
-    if (digit_table_entries(log_r) == 0) return cudaSuccess;
+    const int64_t entries = digit_table_entries(log_r, kind);
+    if (entries == 0) return cudaSuccess;
+    if (kind == 0) {
+        fold_tables_kernel<<<grid_for(entries), 256, 0, s>>>(static_cast<double2 *>(dst), log_r);
+        return cudaGetLastError();
+    }
     const size_t eb = kind == 1 ? 8 : 16;
     const int ns = (log_r + 3) / 4;
     const int l0 = log_r - 4 * (ns - 1);

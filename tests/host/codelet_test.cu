@@ -5,7 +5,9 @@
 // the same sum and against the plain dft16; and the integer power-of-two
 // scaling of the last pass (scale_pow2) bit for bit against the host's
 // IEEE multiplication by 2^k, across normal, subnormal, zero, infinite and
-// NaN inputs.  Compiled by nvcc as host code
+// NaN inputs; and the 16-point codelet whose inputs arrive twiddled
+// (dft16_fma_tw) against the DFT of x_e w_R^(s o e), its stage twiddles
+// encoded here from their definition.  Compiled by nvcc as host code
 // (the codelets are __host__ __device__) and run on the CPU.
 #include <cmath>
 #include <cstdio>
@@ -111,6 +113,47 @@ static bool check_scale()
     return bad == 0;
 }
 
+// the pair (f, r) of twiddle T = c + i d, as dft16_fma_tw reads it
+static double2 fold_pair(long double c, long double d)
+{
+    if (fabsl(c) >= fabsl(d)) return make_double2((double)c, (double)(d / c));
+    return make_double2((double)(4 * d), (double)(c / d));
+}
+
+template <int DIR>
+static bool check_twiddled()
+{
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const int R = 4096;
+    for (int trial = 0; trial < 400; trial++) {
+        // o: random, and every multiple of R/16 (weights that are +-1, +-i)
+        const int o = trial < 16 ? trial * (R / 16) : (int)((uniform() + 1.0) * 0.5 * R) % R;
+        double2 tw[15];
+        for (int h = 1; h < 16; h *= 2)
+            for (int j = 0; j < h; j++) {
+                const long long e = ((long long)o * (8 / h) + (long long)j * (R / (2 * h))) % R;
+                const long double th = -2 * pi * (long double)e / R;  // forward: w_R^e = exp(-2 pi i e / R)
+                tw[h - 1 + j] = fold_pair(cosl(th), sinl(th));
+            }
+        double2 x[16], v[16], y[16];
+        for (int n = 0; n < 16; n++) x[n] = make_double2(uniform(), uniform());
+        // y_e = x_e (w_R^(o e)) in direction DIR, the inputs the codelet stands for
+        for (int e = 0; e < 16; e++) {
+            const long double th = DIR * 2 * pi * (long double)(((long long)o * e) % R) / R;
+            const long double c = cosl(th), sn = sinl(th);
+            y[e] = make_double2((double)(x[e].x * c - x[e].y * sn), (double)(x[e].x * sn + x[e].y * c));
+            v[e] = x[e];
+        }
+        dft16_fma_tw<DIR>(v, tw, 1);
+        const double err = max_err(v, y, 16, DIR);
+        if (!(err <= 2e-15)) {
+            std::printf("dft16_fma_tw dir %d o %d: max error %.3e\n", DIR, o, err);
+            return false;
+        }
+    }
+    return true;
+}
+
 int main()
 {
     bool ok = true;
@@ -120,6 +163,7 @@ int main()
     ok &= check<-1, 4>("dft16 (fma)", 1e-15) && check<1, 4>("dft16 (fma)", 1e-15);
     ok &= check_fma_vs_plain<-1>() && check_fma_vs_plain<1>();
     ok &= check_scale();
+    ok &= check_twiddled<-1>() && check_twiddled<1>();
     if (!ok) return 1;
     std::printf("codelets ok\n");
     return 0;
