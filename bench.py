@@ -402,8 +402,8 @@ def fp64_peak(torch, dev, clocks):
     clock (GB300's FP64 unit count, its nominal 1.25 TFLOP/s) x 2 flop x the
     maximum SM clock (nvidia-smi, sampled with the timed region; 2070 MHz if
     it could not be read).  A probe of independent FP64 chains sustains 84 %
-    of this (1.68 operations per SM per clock), so a kernel bound by the
-    FP64 pipe reads at most about 0.84 here."""
+    of this (1.68 operations per SM per clock); FMA-only code keeps the
+    FP64 pipe up to about 90 % busy."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     return sms * 2 * 2 * mhz * 1e6 / 1e12, (f"FP64 issue peak: {sms} SMs x 2 DFMA/clk x 2 flop x {mhz:g} MHz "
