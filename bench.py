@@ -160,9 +160,11 @@ def source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel: str, workload_key: str):
+def recorded_traffic(kernel: str, workload_key: str, transforms=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current kernel sources; else None.  Records taken on a smaller
+    batch than the bench's launch hold bytes per transform, scaled here by
+    the launch's transforms (the traffic of these passes grows with them)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -172,6 +174,8 @@ def recorded_traffic(kernel: str, workload_key: str):
     e = rec.get(f"{kernel}|{workload_key}")
     if not e or e.get("source_hash") != source_hash():
         return None
+    if transforms is not None and "bytes_per_transform" in e:
+        return int(round(e["bytes_per_transform"] * transforms))
     return e.get("bytes_per_launch")
 
 
@@ -430,12 +434,13 @@ def profiled(M, torch, stream, handles, fn, reps):
     return k, i, cnt, ms / cnt
 
 
-def hbm_roofline(kernel, bytes_per_launch, avg_ms, peaks, what):
+def hbm_roofline(kernel, bytes_per_launch, avg_ms, peaks, what, traffic=None):
     """Roofline record of an HBM-bound kernel: algorithmic bytes per launch
-    over its average launch time, against the HBM copy peak."""
+    over its average launch time, against the HBM copy peak; traffic: the
+    recorded DRAM bytes per launch, when there is a record."""
     gbs = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None, "kernel": kernel,
+            "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": kernel,
             "avg_launch_ms": round(avg_ms, 4), "algorithmic_per_launch": what,
             "peak_source": f"HBM copy peak ({peaks['source']})"}
 
@@ -497,6 +502,8 @@ def measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, pe
                                       "unit": "TFLOP/s", "kernel": f"tile_kernel<dfloat> pass {i} (log2 R = {lr})",
                                       "avg_launch_ms": round(avg, 4),
                                       "algorithmic_per_launch": f"5 flop x {chunk} transforms x 2^{int(math.log2(n))} x {lr} stages",
+                                      "traffic": recorded_traffic(f"df64 pass{i}", f"c128 n=2^{int(math.log2(n))}",
+                                                                  transforms=chunk),
                                       "note": "FP32 issue-bound; no FP64 instruction"}}
         pf.close()
         pi.close()
@@ -544,7 +551,8 @@ def measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, pe
                        "tolerance": 1e-6 * 16 if form == M.FFT_FORM_PLAIN else 1e-5 * 16,
                        "speedup_vs_fp64": round(ms64 / ms, 2), "fp64_ms": round(ms64, 4),
                        "roofline": hbm_roofline(f"{kname} pass {i} (log2 R = {lr})", 2 * chunk * n3 * 8, avg, peaks,
-                                                f"one read + one write of {chunk} transforms x 2^16 x 8 B")}
+                                                f"one read + one write of {chunk} transforms x 2^16 x 8 B",
+                                                recorded_traffic(f"{name} pass{i}", "c64 n=2^16", transforms=chunk))}
         pf.close()
     del xg, xd, yo
     # ---- uneven batch: 20,000 transforms of 2^6..2^16 points
