@@ -172,14 +172,16 @@ static int finish_schedule(Schedule &s, fft_dtype dt, const int *req_width, cons
         if (!last) {
             // rows of the table follow the tile index k, so a warp's
             // consecutive columns b read consecutive weights: the whole
-            // table (mode 2) up to 2^20 (complex128: FP64-bound passes, an
-            // extra complex product costs more than the table's L2 reads) /
-            // 2^12 (complex64: measured, the two small tables of the digit
-            // split stay in L1) entries, else split by the digits of k
+            // table (mode 2) up to 2^24 (complex128: FP64-bound passes use
+            // under 5 % of HBM, so the table's reads -- up to 256 MB, one
+            // entry per point -- cost less than the split's extra complex
+            // product, 4 FP64 instructions per point) / 2^12 (complex64:
+            // measured, the two small tables of the digit split stay in L1)
+            // entries, else split by the digits of k
             // (mode 3), else (passes of < 16 points) the two-level table
             // indexed by b k
             const int lm = exact_log2(p.tw_m);
-            const int direct_max = dt == FFT_C128 ? 20 : 12;
+            const int direct_max = dt == FFT_C128 ? 24 : 12;
             if (lm <= direct_max) p.tw_mode = 2;
             else if (p.log_r >= 4) p.tw_mode = 3;
             else p.tw_lo_bits = (lm + 1) / 2;
