@@ -167,9 +167,10 @@ int fft_exec_adjoint(fft_plan_t p, const void *in, void *out, void *cuda_stream)
 /* As fft_exec, for HOST buffers: `in` and `out` are host pointers (pinned
  * memory gives full copy speed; pageable memory works but copies are
  * staged by the driver).  The batch is streamed through device staging
- * buffers the plan allocates on first use (two slots of up to 64 MiB each):
- * host-to-device copy, transform and device-to-host copy of consecutive
- * slices overlap on the plan's own copy streams.  Stream-ordered: the
+ * buffers the plan allocates on first use (a ring of four slots of 16 MiB,
+ * or one transform where that is larger): host-to-device copy, transform
+ * and device-to-host copy of consecutive slices overlap on the plan's own
+ * copy streams.  Stream-ordered: the
  * copies start after the work already queued on `cuda_stream` (so a call may
  * read the output of the previous host call on that stream), and
  * `cuda_stream` waits for the last copy, so synchronising it makes `out`

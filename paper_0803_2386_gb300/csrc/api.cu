@@ -490,6 +490,12 @@ struct AxisPlan {
     int64_t chunk = 1;
 };
 
+// Staging slots of the host-buffer pipeline (fft_exec_host): slice i uses
+// slot i % kHostSlots, so a slot's next copy in waits only for the transform
+// kHostSlots - 1 slices back (with two slots the copies of one slice had to
+// fit inside the next slice's transform, and often did not).
+constexpr int kHostSlots = 4;
+
 struct fft_plan_s {
     int64_t n = 0, batch = 0;  // n = 0 for an uneven plan
     int64_t total = 0;         // elements in one buffer
@@ -511,16 +517,16 @@ struct fft_plan_s {
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> ev_free;
-    // host-buffer pipeline (fft_exec_host), created on first use
-    DevBuf stage_in[2], stage_out[2];
+    // host-buffer pipeline (fft_exec_host), created on first use: a ring of
+    // kHostSlots staging slots
+    DevBuf stage_in[kHostSlots], stage_out[kHostSlots];
     // per slot: the workspace of multi-pass plans and the stream the slot's
     // transform runs on, so consecutive slices overlap on the GPU
-    DevBuf stage_ws[2];
-    cudaStream_t s_comp[2] = {nullptr, nullptr};
+    DevBuf stage_ws[kHostSlots];
+    cudaStream_t s_comp[kHostSlots] = {};
     int64_t stage_tr = 0;  // transforms per staging slot
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
-                ev_d2h[2] = {nullptr, nullptr};
+    cudaEvent_t ev_h2d[kHostSlots] = {}, ev_comp[kHostSlots] = {}, ev_d2h[kHostSlots] = {};
     cudaEvent_t ev_start = nullptr;  // the caller's stream at the start of a host call
     // uneven plans replay one captured graph per (in, out, adjoint)
     bool use_graph = false;
@@ -735,7 +741,7 @@ static void destroy_plan(fft_plan_s *p)
     dev_free(p->d_queue);
     dev_free(p->d_ctr);
     for (auto &c : p->classes) dev_free(c.d_off);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < kHostSlots; k++) {
         dev_free(p->stage_in[k]);
         dev_free(p->stage_out[k]);
         dev_free(p->stage_ws[k]);
@@ -1589,27 +1595,29 @@ static int setup_staging(fft_plan_t p)
 {
     if (p->stage_tr > 0) return FFT_OK;
     size_t eb = elem_bytes(p->dt);
-    // 64 MiB slots (measured on the bench's complex128 step, 2^20 x 64:
-    // slots of 16 / 32 / 64 / 128 MiB gave 611 / 700 / 701 / 680 GFLOP/s
-    // end to end)
-    const int64_t slot_bytes = (int64_t)64 << 20;
+    // 16 MiB slots (measured on the bench's complex128 step, 2^20 x 64,
+    // 14.17 ms on the device: slots x MiB 2 x 64 16.04 ms end to end, 3 x 64
+    // 15.5, 4 x 64 15.38, 4 x 32 14.80, 8 x 32 14.93, 4 x 16 14.48, 6 x 16
+    // 14.51, 8 x 16 14.50)
+    const int64_t slot_bytes = (int64_t)16 << 20;
     int64_t tr = std::max<int64_t>(1, slot_bytes / (p->n * (int64_t)eb));
     tr = std::min(tr, p->batch);
     size_t bytes = (size_t)tr * p->n * eb;
     const SizeClass &C = p->classes[0];
     const bool needs_ws = C.sched.unblocked || C.sched.npass > 1;
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < kHostSlots; k++) {
         int st = dev_alloc(p->stage_in[k], bytes, "host staging (in)");
         if (st == FFT_OK) st = dev_alloc(p->stage_out[k], bytes, "host staging (out)");
         if (st == FFT_OK && needs_ws) st = dev_alloc(p->stage_ws[k], bytes, "host staging (workspace)");
         if (st != FFT_OK) return st;
     }
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamCreateWithFlags(&p->s_comp[k], cudaStreamNonBlocking);
+    for (int k = 0; k < kHostSlots && e == cudaSuccess; k++)
+        e = cudaStreamCreateWithFlags(&p->s_comp[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
-    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    for (int k = 0; k < kHostSlots && e == cudaSuccess; k++) {
         e = cudaEventCreateWithFlags(&p->ev_h2d[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_d2h[k], cudaEventDisableTiming);
@@ -1619,7 +1627,7 @@ static int setup_staging(fft_plan_t p)
     return FFT_OK;
 }
 
-// Slice i uses slot i % 2: H2D on s_h2d, transform on the slot's stream
+// Slice i uses slot i % kHostSlots: H2D on s_h2d, transform on the slot's stream
 // s_comp[k] (so one slice's last wave overlaps the next slice's first), D2H
 // on s_d2h; events order the reuse of each slot, and the caller's stream
 // waits for the last copies out.
@@ -1636,7 +1644,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
     const int sign = direction_sign(p, false);
     size_t eb = elem_bytes(p->dt);
     cudaStream_t cs = (cudaStream_t)stream;
-    bool used[2] = {false, false};
+    bool used[kHostSlots] = {};
     const SizeClass &C = p->classes[0];
     // stream order: the copies start after the work already queued on the
     // caller's stream (for instance a previous host call whose output this
@@ -1644,7 +1652,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
     {
         cudaError_t e = cudaEventRecord(p->ev_start, cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_h2d, p->ev_start, 0);
-        for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(p->s_comp[k], p->ev_start, 0);
+        for (int k = 0; k < kHostSlots && e == cudaSuccess; k++) e = cudaStreamWaitEvent(p->s_comp[k], p->ev_start, 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (stream order)");
     }
     // Slices of stage_tr transforms, ramped at both ends (from an eighth of a
@@ -1671,7 +1679,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
     }
     int64_t b0 = 0;
     for (size_t i = 0; i < slices.size(); b0 += slices[i], i++) {
-        int k = (int)(i & 1);
+        int k = (int)(i % kHostSlots);
         int64_t cnt = slices[i];
         size_t off = (size_t)b0 * p->n * eb, bytes = (size_t)cnt * p->n * eb;
         cudaError_t e = cudaSuccess;
@@ -1695,7 +1703,7 @@ static int run_host(fft_plan_t p, const void *in, void *out, void *stream)
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (copy out)");
         used[k] = true;
     }
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < kHostSlots; k++) {
         if (!used[k]) continue;
         cudaError_t e = cudaStreamWaitEvent(cs, p->ev_d2h[k], 0);
         if (e != cudaSuccess) return fail_cuda(e, "fft_exec_host (join)");
