@@ -1,6 +1,7 @@
 // df64.cuh -- double-float arithmetic: a real number carried as the
-// unevaluated sum hi + lo of two floats (|lo| < ulp(hi)), about 48
-// significant bits, computed entirely on the FP32 pipes.
+// unevaluated sum hi + lo of two floats (|lo| about ulp(hi) or below, at
+// most half of it after df_norm), about 48 significant bits, computed
+// entirely on the FP32 pipes.
 //
 // GB300 executes FP64 at about 1/58 of its FP32 rate (measured), so an
 // FFT in native FP64 is bound by the FP64 issue rate at ~4 % of HBM.  The
