@@ -357,8 +357,10 @@ __host__ __device__ __forceinline__ void dft16_fma(double2 *v)
 // form.  With (a, b) = (q.re, q.im) for the first form and (q.im, q.re) for
 // the second, both forms give T q = f (t1 + i t2) from the same two FMAs,
 // t1 = a - r b and t2 = r a + b, except that the second form's t1 comes out
-// negated (DIR = +1, conjugating T: its t2) -- so instead of negating it,
-// the butterfly swaps which of its outputs takes + f t1 and which - f t1.
+// negated -- so instead of negating it, the butterfly swaps which of its
+// outputs takes + f t1 and which - f t1.  DIR = +1 conjugates T: r changes
+// sign (t1 = a + r b, t2 = b - r a), and it is the second form's t2 that
+// comes out negated and whose outputs swap.
 // The decoding and the swaps are integer operations (exponent bits,
 // selects): a negation written in the code becomes an FP64 instruction, so
 // none is, and only the 6 fused multiply-adds reach the FP64 pipe.
