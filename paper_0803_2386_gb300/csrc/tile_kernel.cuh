@@ -486,20 +486,24 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
 }
 
-// The double-float tile of 2^(4 NS) points (NS radix-16 digits), arranged
-// so that one copy of the digit's code serves every digit: the same steps
-// as tile_load + tile_finish, with shared memory standing in for the
-// register array wherever a loop would index it.  A double-float digit is
+// The double-float tile (2^4 .. 2^12 points: a first digit of E0 = 2, 4, 8
+// or 16 points, then radix-16 digits), arranged so that one copy of the
+// radix-16 digit's code serves every such digit: the same steps as
+// tile_load + tile_finish, with shared memory standing in for the register
+// array wherever a loop would index it.  A double-float digit is
 // about 1,300 instructions, so the unrolled form (a copy per digit, and
 // the conversions and weights of all 16 points inlined at the load and the
 // store) outgrows the instruction cache.
-//   1. HBM -> shared memory: the thread's 16 first-digit points, as raw
-//      complex128 by asynchronous 16-byte copies, all in flight at once;
+//   1. HBM -> shared memory: the thread's 16 first-digit points (its
+//      16 / E0 codelets of E0 points), as raw complex128 by asynchronous
+//      16-byte copies, all in flight at once;
 //   2. each thread converts its own points to double-float in place;
-//   3. the digits, one loop body: read 16 points, codelet, weights, write
-//      back (renormalised), barrier -- the first digit reads the thread's
-//      own points, the last leaves its results at the thread's own
-//      positions, so neither needs a barrier before it;
+//   3. a first digit of fewer than 16 points on its own (the thread's
+//      codelets, their weights, write back, barrier); then the radix-16
+//      digits, one loop body: read 16 points, codelet, weights, write back
+//      (renormalised), barrier -- a first digit reads the thread's own
+//      points, the last leaves its results at the thread's own positions,
+//      so neither needs a barrier before it;
 //   4. stores: the thread's 16 results from shared memory, with the pass
 //      weights (non-last pass) or the scale and final transpose (last
 //      pass), converted back to complex128.
@@ -509,44 +513,72 @@ __device__ __forceinline__ void tile_body_df(const PassArgs &p, const int64_t ct
     using V = dcplx;
     using M = MemOf<dfloat>;
     constexpr int R = 1 << LOGR;
-    constexpr int NS = LOGR / 4;
+    constexpr int NS = (LOGR + 3) / 4;       // digits
+    constexpr int L0 = LOGR - 4 * (NS - 1);  // log2 of the first digit's radix
+    constexpr int E0 = 1 << L0;
+    constexpr int G0 = 16 / E0;              // first-digit codelets per thread
+    constexpr int Q0 = R / E0;
     constexpr int U = R / 16;  // threads per column
-    static_assert(LOGR % 4 == 0 && NS >= 2 && NS <= 3, "radix-16 digits");
+    static_assert(LOGR >= 4 && LOGR <= 12, "tile size");
     const int tid = threadIdx.x;
     const int w = tid % W;
     const int u = tid / W;
     const TileRef r = tile_ref<dfloat, LOGR, LAST, W>(p, cta);
     const bool valid = r.valid;
 
-    // ---- 1. raw points m = e U + u of column w
+    // ---- 1. raw points m = e Q0 + g U + u of column w (codelet g, input e)
     {
         const double2 *in = reinterpret_cast<const double2 *>(p.in) + r.base;
         const int64_t mstride = LAST ? 1 : p.B;
 #pragma unroll
-        for (int e = 0; e < 16; e++) {
-            const int m = e * U + u;
-            V *slot = &tile[tpad(m) * W + w];
-            if (valid) cp_async16(slot, in + (int64_t)m * mstride);
-            else *slot = V{};
-        }
+        for (int g = 0; g < G0; g++)
+#pragma unroll
+            for (int e = 0; e < E0; e++) {
+                const int m = e * Q0 + g * U + u;
+                V *slot = &tile[tpad(m) * W + w];
+                if (valid) cp_async16(slot, in + (int64_t)m * mstride);
+                else *slot = V{};
+            }
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     }
     // ---- 2. complex128 -> double-float, in place (not for the (hi, lo)
     // pairs an earlier pass left in the workspace)
     if (!p.df_in) {
 #pragma unroll 2
-        for (int e = 0; e < 16; e++) {
-            V *slot = &tile[tpad(e * U + u) * W + w];
+        for (int i = 0; i < 16; i++) {
+            V *slot = &tile[tpad((i % E0) * Q0 + (i / E0) * U + u) * W + w];
             *slot = dc_from(*reinterpret_cast<const double2 *>(slot));
         }
     }
-    // ---- 3. the radix-16 digits
     const V *twd = reinterpret_cast<const V *>(p.tw_digit);  // weights between digits, rows by k
     V v[16];
     int S = R;
     int doff = 0;  // this digit level's table
+    // ---- 3a. a first digit of fewer than 16 points: the thread's G0
+    // codelets, weights w_R^(mq k) (mq = g U + u), written back in place
+    if constexpr (E0 < 16) {
+#pragma unroll
+        for (int g = 0; g < G0; g++) {
+            const int mq = g * U + u;
+#pragma unroll
+            for (int e = 0; e < E0; e++) v[e] = tile[tpad(e * Q0 + mq) * W + w];
+            if (valid) {
+                dft_codelet<DIR, L0>(v);
+                if constexpr (NS > 1) {
+#pragma unroll
+                    for (int k = 1; k < E0; k++) v[k] = c_tw<DIR>(v[k], M::ldg(twd + k * Q0 + mq));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < E0; k++) tile[tpad(k * Q0 + mq) * W + w] = M::norm(v[k]);
+        }
+        S = Q0;
+        doff = R;
+        if constexpr (NS > 1) __syncthreads();
+    }
+    // ---- 3b. the radix-16 digits
 #pragma unroll 1
-    for (int j = 0; j < NS; j++) {
+    for (int j = E0 < 16 ? 1 : 0; j < NS; j++) {
         const int Q = S / 16;
         const int pre = u / Q, mq = u % Q;
         const int pos0 = pre * S + mq;
@@ -610,7 +642,7 @@ __global__ void __launch_bounds__(tile_threads(LOGR), tile_min_blocks<T>(LOGR))
     using V = typename cvec<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t cta = (int64_t)blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
-    if constexpr (std::is_same<T, dfloat>::value && LOGR % 4 == 0 && LOGR >= 8)
+    if constexpr (std::is_same<T, dfloat>::value)
         tile_body_df<DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));
     else
         tile_body<T, DIR, LOGR, LAST, tile_width(LOGR)>(p, cta, reinterpret_cast<V *>(smem_raw));

@@ -9,7 +9,8 @@ template <int DIR, int LOGR, bool LAST>
 static cudaError_t launch_df_one(const PassArgs &a, cudaStream_t s)
 {
     constexpr int W = tile_width(LOGR);
-    constexpr size_t smem = LOGR >= 5 ? (size_t)((1 << LOGR) + (1 << LOGR) / 16) * W * sizeof(dcplx) : 0;
+    // every double-float tile stages its points in shared memory (tile_body_df)
+    constexpr size_t smem = (size_t)((1 << LOGR) + (1 << LOGR) / 16) * W * sizeof(dcplx);
     static DeviceOnce setup;
     cudaError_t e = smem_setup(setup, tile_kernel<dfloat, DIR, LOGR, LAST>, smem, tile_min_blocks<dfloat>(LOGR));
     if (e != cudaSuccess) return e;
