@@ -891,6 +891,14 @@ extern "C" int fft_plan_ex(fft_plan_t *out, int64_t n, int64_t batch, fft_dtype 
         st = build_schedule(c.sched, n, dt, lat.c_str(), &req_chunk);
     }
     if (st == FFT_OK && form == FFT_FORM_DF64) {
+        // double-float passes are latency-bound, not FP64-bound: beyond 2^20
+        // entries the whole table's DRAM reads cost them more than the digit
+        // split's complex product (2^24: first pass 0.35 against 0.25 ms
+        // for the others), so they keep the split
+        for (int i = 0; i + 1 < c.sched.npass; i++) {
+            PassDesc &d = c.sched.pass[i];
+            if (d.tw_mode == 2 && exact_log2(d.tw_m) > 20 && d.log_r >= 4) d.tw_mode = 3;
+        }
         bool ok = !c.sched.unblocked && c.sched.npass > 0;
         for (int i = 0; ok && i < c.sched.npass; i++) {
             const PassDesc &d = c.sched.pass[i];
