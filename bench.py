@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the other forms (df64, precision, uneven, adjoint)")
     ap.add_argument("--sweep", default="", help="comma-separated log2 n list: extra lines to stderr")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the size sweep (n = 2^12..2^24) the JSON line carries under \"sweep\"")
     ap.add_argument("--case", default="", choices=["", "c1", "c64", "c64_cluster", "c64_rows", "tc_fp16", "tc_bf16", "tc32", "c64_256", "c128", "df64", "dm", "nd2d"],
                     help="small profiling case, three runs: complex64 n=2^16 batch 512 forward "
                          "(c64, tc_*), or complex128 n=2^20 batch 16 forward (c128, df64)")
@@ -359,6 +361,11 @@ def run_moafft(args):
         e2e = measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, world, args)
     forms = (measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, peaks)
              if rank == 0 and not args.no_forms else None)
+    sweep = None
+    if rank == 0 and not args.no_sweep and args.log2n == 20 and args.batch == 0:
+        # the same step across the sizes the configuration sweeps, 2^12..2^24
+        sweep = {"config": "c128 FP64, forward + inverse, n * batch = 2^26 (1 GiB per buffer), CUDA events",
+                 "points": [sweep_line(M, torch, dev, stream, t, args, quiet=True) for t in range(12, 25, 2)]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -367,7 +374,7 @@ def run_moafft(args):
                 "data": "synthetic (seeded uniform[-1,1], seed = rank)",
                 "config": config(n, batch, world), "gpu_launches": launches,
                 "roundtrip_rel_err": rt, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-                "forms": forms}
+                "forms": forms, "sweep": sweep}
         if world == 1 and not args.no_cpu_baseline:
             fwd.exec(x, X, stream)  # the timed forward spectrum (deterministic)
             torch.cuda.synchronize()
@@ -646,7 +653,10 @@ def measure_e2e(M, torch, fwd, inv, x, stream, dev, barrier, dist, n, batch, wor
     return e2e
 
 
-def sweep_line(M, torch, dev, stream, log2n, args):
+def sweep_line(M, torch, dev, stream, log2n, args, quiet=False):
+    """The headline step (complex128 FP64, forward + inverse, n * batch =
+    2^26) at n = 2^log2n: GFLOP/s from CUDA events over max(1, steps / 2)
+    steps after two warm-up steps, and the round-trip error."""
     n, batch = workload(log2n)
     gen = torch.Generator(device=dev).manual_seed(log2n)
     x = torch.rand(batch, n, dtype=torch.complex128, device=dev, generator=gen) * 2 - (1 + 1j)
@@ -669,12 +679,13 @@ def sweep_line(M, torch, dev, stream, log2n, args):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / k
     rt = (torch.linalg.vector_norm((y - x).flatten()) / torch.linalg.vector_norm(x.flatten())).item()
-    print(json.dumps({"sweep": True, "n": n, "batch": batch, "ms_per_step": round(ms, 4),
-                      "gflops": round(flops_per_step(n, batch) / (ms * 1e-3) / 1e9, 2),
-                      "roundtrip_rel_err": rt}),
-          file=sys.stderr, flush=True)
+    row = {"n": n, "batch": batch, "ms_per_step": round(ms, 4),
+           "gflops": round(flops_per_step(n, batch) / (ms * 1e-3) / 1e9, 2), "roundtrip_rel_err": rt}
+    if not quiet:
+        print(json.dumps(dict(sweep=True, **row)), file=sys.stderr, flush=True)
     fwd.close()
     inv.close()
+    return row
 
 
 def _time(torch, stream, fn, reps, warm=2):
