@@ -467,7 +467,9 @@ def measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, pe
     """The library's other forms, each timed on this GPU with its dominant
     kernel's roofline (measured with CUDA events around every launch, as the
     headline's):
-      df64        the headline step in double-float butterflies (FP32 pipes);
+      df64        the headline step in double-float butterflies (FP32 pipes),
+                  with its error against the FP64 path and against the FP64
+                  oracle on three sampled transforms;
       fp32, tc_fp16, tc_bf16
                   complex64 n = 2^16, batch 4096, forward (the precision
                   configuration), Gaussian sigma = 1 input, with the error
@@ -497,6 +499,9 @@ def measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, pe
 
         ms = _time(torch, stream, step, reps, warm=2)
         err = (torch.linalg.vector_norm((y - X).flatten()) / torch.linalg.vector_norm(X.flatten())).item()
+        # three sampled transforms against the FP64 oracle (y: the timed forward output)
+        dpicks = [0, batch // 2, batch - 1]
+        err_oracle = oracle_rows_err(O, np, y[dpicks].cpu().numpy(), x[dpicks].cpu().numpy(), "forward")
         k, i, cnt, avg = profiled(M, torch, stream, [pf.handle, pi.handle], step, 2)
         desc = json.loads((pf if k == 0 else pi).describe())
         lr = desc["schedule"]["passes"][i]["log_r"]
@@ -504,7 +509,8 @@ def measure_forms(M, torch, x, X, stream, n, batch, world, args, dev, clocks, pe
         fl = 5.0 * chunk * n * lr
         forms["df64"] = {"value": round(flops_per_step(n, batch) * world / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
                          "ms_per_step": round(ms, 4), "dtype": "f32x2 (double-float)",
-                         "rel_err_vs_fp64_path": err, "tolerance": 1e-12,
+                         "rel_err_vs_fp64_path": err,
+                         "rel_err_vs_oracle": {"max": err_oracle, "transforms": len(dpicks)}, "tolerance": 1e-12,
                          "roofline": {"bound": "alu", "achieved": round(fl / (avg * 1e-3) / 1e12, 4),
                                       "unit": "TFLOP/s", "kernel": f"tile_kernel<dfloat> pass {i} (log2 R = {lr})",
                                       "avg_launch_ms": round(avg, 4),
